@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the TreeCode hot path on GB300.
+
+One step = one kick-drift-kick leapfrog step (Eqs. 2-5) of the whole hot
+path: kick+drift+box, Morton keys, onesweep sort, octree, gather, FP64
+moments, FP32 tree walk with the fused force write-back and final kick, and
+the FP64 diagnostics reductions.  Workload: the galaxy-like model at
+N = 1e8 (exponential disk 60 %, Hernquist bulge 10 %, truncated NFW-like
+halo 30 %), eps = 0.02, theta = 0.7, quadrupole cells, leaf <= 16, groups of
+32, tau = 0.002, FP32 with Kahan-compensated sums.  Inputs are seeded
+synthetic particles, resident in HBM, 4+ GB (far larger than L2).
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the
+host cores instead (a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "tree-force particles/s at N=1e8 θ=0.7, FP32 vs FP64 GPU at force err ≤1e-3"
+UNIT = "particles/s"
+SEED = 20241202
+PARAMS = dict(eps=0.02, theta=0.7, order=2, leaf_cap=16, group_size=32, kahan=1)
+TAU = 0.002
+WORKLOAD = ("galaxy-like N=1e8: exp. disk 60% (R_d=1, z0=0.1) + Hernquist bulge 10% (a=0.2) + "
+            "NFW-like halo 30% (r_s=5, r_t=50), eps=0.02, theta=0.7, quadrupole, leaf<=16, "
+            "KDK tau=0.002")
+# Algorithmic flop counts per pair (FMA = 2 flops; rsqrt = 1): PP with
+# potential 20, PC quadrupole 54, PC monopole 20.
+FLOPS_PP, FLOPS_PC_QUAD, FLOPS_PC_MONO = 20, 54, 20
+# FP32 peak derived from unit counts and clocks: 152 SMs x 128 FP32 lanes x
+# 2 flops (FMA) x 2.070 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# DRAM bytes per walk launch from ncu (dram__bytes_read.sum + write.sum) on a
+# smaller case of the same kernel, per particle; None when the kernel has
+# changed since the counters were taken.
+WALK_DRAM_BYTES_PER_PARTICLE = None
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=float, default=1e8)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 20,
+                    help="particles of the oracle's bounded sample (same galaxy recipe)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the main leg only (no FP64 leg, error check, e2e, CPU baseline)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1])); mx.append(float(r[2]))
+                for nm, val in zip(names, r[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2412_01733_gb300 import build, inputs, treegb
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    n = int(a.n)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # each rank runs its own replica of the workload (independent seeds)
+    x, v, m = inputs.galaxy(n, SEED + rank, device=dev, dtype=torch.float32)
+    x, v, m = x.contiguous(), v.contiguous(), m.contiguous()
+    ws = treegb.Workspace(n, **PARAMS)
+    acc, phi = ws.accel(x, m)
+    diag = torch.empty(8, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ws.leapfrog_step(x, v, m, acc, TAU, phi=phi)
+        ws.diagnostics(x, v, m, phi, out=diag)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws.status() != 0:
+        raise RuntimeError("device status set during warm-up")
+    d0 = diag.cpu().numpy().copy()
+
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    ws.timing(True)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    t = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    phases, launches = ws.timing_read()
+    ws.timing(False)
+    inf = ws.info()
+    st = ws.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} in the timed region")
+    d1 = diag.cpu().numpy().copy()
+    value = world * n * a.steps / t
+
+    # roofline of the dominant kernel: the FP32 walk
+    walk_ms, walk_calls = phases["walk"]
+    walk_s = walk_ms / 1e3 / max(walk_calls, 1)
+    flops = FLOPS_PP * inf["pp_pairs"] + FLOPS_PC_QUAD * inf["pc_pairs"]
+    achieved = flops / walk_s / 1e12
+    traffic = None if WALK_DRAM_BYTES_PER_PARTICLE is None else WALK_DRAM_BYTES_PER_PARTICLE * n
+    roofline = {"bound": "alu", "kernel": "k_walk<float,1,quad,kahan,soft,force>", "achieved": achieved,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": traffic,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz (no FP32 entry in MEASURED_PEAKS)",
+                "flops_per_launch": flops, "pp_pairs": inf["pp_pairs"], "pc_pairs": inf["pc_pairs"],
+                "walk_ms": walk_s * 1e3}
+    step_ms = t * 1e3 / a.steps
+    breakdown = {k: round(ms / a.steps, 3) for k, (ms, c) in phases.items() if c}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": n, "group_size": PARAMS["group_size"],
+                      "leaf_cap": PARAMS["leaf_cap"], "kahan": True, "parallelism": f"replicas{world}",
+                      "l2": "inputs (4+ GB) larger than L2 (129 MB)"},
+           "gpu_launches": launches, "roofline": roofline, "phase_ms_per_step": breakdown,
+           "interactions_per_s": world * (inf["pp_pairs"] + inf["pc_pairs"]) / walk_s,
+           "interactions_per_particle": (inf["pp_pairs"] + inf["pc_pairs"]) / n,
+           "tree": {"nodes": inf["n_nodes"], "depth": inf["depth"], "max_stack": inf["max_stack"]},
+           "energy_rel_drift": float(abs((d1[0] + d1[1]) - (d0[0] + d0[1])) / abs(d0[0] + d0[1])),
+           "clocks": ck}
+
+    if not a.no_extras:
+        # force error of the FP32 tree against the GPU direct sum (4096 sampled particles)
+        g = torch.Generator().manual_seed(SEED)
+        tgt = torch.randint(0, n, (4096,), generator=g)
+        ad, _ = ws.direct(x, m, tgt, precision="f32")
+        at = acc[:, tgt.to(dev)].double()
+        err = ((at - ad).norm(dim=0) / ad.norm(dim=0)).cpu()
+        out["force_err_vs_direct"] = {"median": float(err.median()), "p99": float(err.quantile(0.99)),
+                                      "max": float(err.max()), "samples": 4096,
+                                      "reference": "GPU direct sum, FP32 pairs, compensated, FP64 chunk totals"}
+        # same-GPU FP64 plain path: one force evaluation (build + moments + walk) on the same state
+        x64, m64 = x.double().contiguous(), m.double().contiguous()
+        del ad
+        torch.cuda.synchronize()
+        ws64 = treegb.Workspace(n, precision="f64", **{k: v for k, v in PARAMS.items() if k != "kahan"})
+        ws64.accel(x64, m64)
+        ws64.timing(True)
+        f0 = torch.cuda.Event(enable_timing=True); f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        a64, p64 = ws64.accel(x64, m64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ph64, _ = ws64.timing_read()
+        t64 = f0.elapsed_time(f1) / 1e3
+        ws.timing(True)
+        g0 = torch.cuda.Event(enable_timing=True); g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        a32, p32 = ws.accel(x, m)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        ph32, _ = ws.timing_read()
+        ws.timing(False)
+        t32 = g0.elapsed_time(g1) / 1e3
+        e64 = ((a32.double()[:, tgt.to(dev)] - a64[:, tgt.to(dev)]).norm(dim=0)
+               / a64[:, tgt.to(dev)].norm(dim=0)).cpu()
+        out["fp32_vs_fp64"] = {"fp32_force_particles_per_s": n / t32, "fp64_force_particles_per_s": n / t64,
+                               "speedup": t64 / t32, "fp32_walk_ms": ph32["walk"][0],
+                               "fp64_walk_ms": ph64["walk"][0],
+                               "fp32_vs_fp64_median_rel": float(e64.median()),
+                               "fp32_vs_fp64_max_rel": float(e64.max())}
+        del ws64, x64, m64, a64, p64, a32, p32
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        # end to end through the C ABI with host-resident state
+        xh = x.cpu().pin_memory(); vh = v.cpu().pin_memory(); mh = m.cpu().pin_memory()
+        ah = acc.cpu().pin_memory(); dh = torch.empty(8, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            x.copy_(xh, non_blocking=True); v.copy_(vh, non_blocking=True)
+            m.copy_(mh, non_blocking=True); acc.copy_(ah, non_blocking=True)
+            ws.leapfrog_step(x, v, m, acc, TAU, phi=phi)
+            ws.diagnostics(x, v, m, phi, out=diag)
+            xh.copy_(x, non_blocking=True); vh.copy_(v, non_blocking=True)
+            ah.copy_(acc, non_blocking=True); dh.copy_(diag, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        h0 = torch.cuda.Event(enable_timing=True); h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(a.steps):
+            e2e_step()
+        h1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        te = max_over_ranks(h0.elapsed_time(h1) / 1e3)
+        out["e2e"] = {"value": world * n * a.steps / te, "unit": UNIT,
+                      "h2d_bytes_per_step": 40 * n, "d2h_bytes_per_step": 36 * n + 64}
+        # the FP64 CPU oracle on the host cores, bounded sample, rank 0 at N = 1 only
+        if world == 1:
+            out["cpu_baseline"] = cpu_baseline(a.cpu_sample)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(ns):
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2412_01733_gb300 import inputs
+    x, _, m = inputs.galaxy(ns, SEED, dtype=torch.float64)
+    x, m = x.numpy(), m.numpy()
+    t0 = time.perf_counter()
+    O.tree_forces(x, m, eps=PARAMS["eps"], theta=PARAMS["theta"], lcap=PARAMS["leaf_cap"],
+                  gs=PARAMS["group_size"], quad=True)
+    t = time.perf_counter() - t0
+    return {"value": ns / t, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+            "sample": f"one FP64 tree-force evaluation (box, keys, sort, octree, moments, lists, forces) "
+                      f"of the same galaxy recipe at N={ns} (not 1e8); {t:.2f} s"}
+
+
+# ----------------------------------------------------------------- reference arm (the oracle)
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2412_01733_gb300 import inputs
+    ns = a.cpu_sample
+    x, v, m = inputs.galaxy(ns, SEED, dtype=torch.float64)
+    x, v, m = x.numpy(), v.numpy(), m.numpy()
+    acc = lambda xx: O.tree_accel(xx, m, eps=PARAMS["eps"], theta=PARAMS["theta"], lcap=PARAMS["leaf_cap"],
+                                  gs=PARAMS["group_size"], quad=True)
+    st = acc(x)
+    for _ in range(a.warmup):
+        x, v, aa, ph = O.kdk(x, v, m, TAU, 1, acc, a0=st)
+        st = (aa, ph)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        x, v, aa, ph = O.kdk(x, v, m, TAU, 1, acc, a0=st)
+        st = (aa, ph)
+    t = time.perf_counter() - t0
+    value = ns * a.steps / t
+    sample = (f"FP64 CPU oracle KDK steps (tree rebuilt each step) of the same galaxy recipe at N={ns} "
+              f"(bounded sample of the N=1e8 workload)")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3 / a.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": ns, "parallelism": "host threads"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

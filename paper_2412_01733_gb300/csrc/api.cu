@@ -1,0 +1,553 @@
+// api.cu -- the C ABI (include/treegb.h): workspace management, argument
+// checks, call sequencing and the host-side opening-criterion table.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+
+using namespace treegb;
+
+namespace {
+
+#define TRY_CUDA(expr)                              \
+    do {                                            \
+        cudaError_t e_ = (expr);                    \
+        if (e_ != cudaSuccess) return TREE_ERR_CUDA; \
+    } while (0)
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+tree_status_t check_params(const TreeParams *p) {
+    if (!p) return TREE_ERR_ARG;
+    if (!(p->eps >= 0.0) || !isfinite(p->eps)) return TREE_ERR_ARG;
+    if (!(p->theta >= 0.0) || !isfinite(p->theta)) return TREE_ERR_ARG;
+    if (!isfinite(p->G)) return TREE_ERR_ARG;
+    if (p->order != 0 && p->order != 2) return TREE_ERR_ARG;
+    if (p->leaf_cap < 1 || p->leaf_cap > 16) return TREE_ERR_ARG;
+    if (p->group_size != 16 && p->group_size != 32 && p->group_size != 64) return TREE_ERR_ARG;
+    if (p->stack_depth < 256 || p->stack_depth > 8192 || p->stack_depth % 32) return TREE_ERR_ARG;
+    if (p->precision != TREE_F32 && p->precision != TREE_F64) return TREE_ERR_ARG;
+    if (p->kahan != 0 && p->kahan != 1) return TREE_ERR_ARG;
+    if (p->node_cap < 0 || p->node_cap >= kMaxNodes) return TREE_ERR_ARG;
+    return TREE_OK;
+}
+
+// D_l = min{ d >= 0 : s_l^2 < fl(theta^2 * d) }, s_l = 2^(21-l); fl(theta^2 d) is
+// non-decreasing in d, so a binary search over the exact predicate finds it.
+// Group-cell distances satisfy d2 <= 3 (2^21)^2 < 2^44, so thresholds above
+// that never accept.
+void mac_table(double theta, int64_t *D) {
+    const double th2 = theta * theta;
+    const int64_t never = INT64_MAX;
+    for (int l = 0; l < kLevels; ++l) {
+        const int64_t s = (int64_t)1 << (kBits - l);
+        const double s2 = (double)(s * s);
+        if (!(th2 > 0.0)) { D[l] = never; continue; }
+        int64_t lo = 0, hi = (int64_t)1 << 50;  // predicate false at lo=0 (s2 > 0), test hi
+        if (!(s2 < th2 * (double)hi)) { D[l] = never; continue; }
+        while (hi - lo > 1) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (s2 < th2 * (double)mid) hi = mid;
+            else lo = mid;
+        }
+        D[l] = hi;
+    }
+}
+
+int64_t default_node_cap(int64_t n_max, int leaf_cap) {
+    // About 1.2 nodes per leaf-capacity worth of particles, with generous slack;
+    // the build degrades gracefully (TREE_DEV_NODES) if a distribution needs more.
+    double c = (double)n_max * (8.0 / (leaf_cap + 1.0) + 0.25) + 4096.0;
+    if (c > (double)(kMaxNodes - 1)) c = (double)(kMaxNodes - 1);
+    return (int64_t)c;
+}
+
+void free_all(TreeWorkspace *ws) {
+    void *ptrs[] = {ws->key, ws->key_alt, ws->idx, ws->idx_alt, ws->hist, ws->sort_status, ws->level_status,
+                    ws->ctr, ws->part, ws->box, ws->spos, ws->nfirst, ws->ncount, ws->ngeo, ws->nlink,
+                    ws->mom64, ws->mom_a, ws->mom_b, ws->mom_c, ws->dstatus, ws->stats, ws->gstat,
+                    ws->list_cnt, ws->pc_list, ws->pp_list, ws->direct_part, ws->dmac};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : ws->ev) cudaEventDestroy(e);
+    ws->ev.clear();
+    ws->ev_phase.clear();
+}
+
+template <typename T>
+bool dalloc(T **p, size_t count) {
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, count * sizeof(T)) == cudaSuccess;
+}
+
+// Records a (start, stop) event pair around one phase when timing is on.
+struct PhaseScope {
+    TreeWorkspace *ws;
+    cudaStream_t s;
+    size_t pair = SIZE_MAX;
+    int64_t l0 = 0;
+    PhaseScope(TreeWorkspace *w, int phase, cudaStream_t st) : ws(w), s(st) {
+        if (!ws->timing) return;
+        l0 = ws->launches;
+        if (ws->ev_used == ws->ev_phase.size()) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess) return;
+            if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+            ws->ev.push_back(a);
+            ws->ev.push_back(b);
+            ws->ev_phase.push_back(phase);
+        }
+        pair = ws->ev_used++;
+        ws->ev_phase[pair] = phase;
+        cudaEventRecord(ws->ev[2 * pair], s);
+    }
+    ~PhaseScope() {
+        if (pair == SIZE_MAX) return;
+        cudaEventRecord(ws->ev[2 * pair + 1], s);
+        ws->timed_launches += ws->launches - l0;
+    }
+};
+
+tree_status_t upload_mac(TreeWorkspace *ws, cudaStream_t s) {
+    if (ws->mac_theta != ws->p.theta) {
+        mac_table(ws->p.theta, ws->mac_D);
+        ws->mac_theta = ws->p.theta;
+        // synchronous copy from pageable host memory: the table is 176 bytes
+        TRY_CUDA(cudaMemcpyAsync(ws->dmac, ws->mac_D, sizeof(ws->mac_D), cudaMemcpyHostToDevice, s));
+        TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    return TREE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tree_version(void) { return "treegb 0.1"; }
+
+const char *tree_status_string(tree_status_t s) {
+    switch (s) {
+        case TREE_OK: return "ok";
+        case TREE_ERR_ARG: return "invalid argument";
+        case TREE_ERR_CUDA: return "CUDA runtime error";
+        case TREE_ERR_ALLOC: return "device allocation failed";
+        case TREE_ERR_CAPACITY: return "n exceeds the workspace capacity";
+        case TREE_ERR_STATE: return "call order violated";
+        case TREE_ERR_DEVICE: return "device status word is set";
+    }
+    return "unknown status";
+}
+
+tree_status_t tree_params_default(TreeParams *p) {
+    if (!p) return TREE_ERR_ARG;
+    p->G = 1.0;
+    p->eps = 0.01;
+    p->theta = 0.7;
+    p->order = 2;
+    p->leaf_cap = 16;
+    p->group_size = 32;
+    p->stack_depth = 1024;
+    p->precision = TREE_F32;
+    p->kahan = 1;
+    p->node_cap = 0;
+    return TREE_OK;
+}
+
+tree_status_t tree_mac_table(double theta, int64_t *D) {
+    if (!D || !(theta >= 0.0) || !isfinite(theta)) return TREE_ERR_ARG;
+    mac_table(theta, D);
+    return TREE_OK;
+}
+
+tree_status_t tree_workspace_create(int64_t n_max, const TreeParams *p, TreeWorkspace **out) {
+    if (!out) return TREE_ERR_ARG;
+    *out = nullptr;
+    tree_status_t st = check_params(p);
+    if (st != TREE_OK) return st;
+    if (n_max < 0 || n_max >= (int64_t)kValMask) return TREE_ERR_ARG;
+    TreeWorkspace *ws = new (std::nothrow) TreeWorkspace();
+    if (!ws) return TREE_ERR_ALLOC;
+    ws->p = *p;
+    if (cudaGetDevice(&ws->device) != cudaSuccess) { delete ws; return TREE_ERR_CUDA; }
+    ws->n_max = n_max;
+    ws->node_cap = p->node_cap > 0 ? p->node_cap : default_node_cap(n_max, p->leaf_cap);
+    ws->real_size = p->precision == TREE_F64 ? 8 : 4;
+    const size_t N = (size_t)(n_max > 0 ? n_max : 1);
+    const size_t NC = (size_t)ws->node_cap;
+    ws->sort_tiles_max = (n_max + kSortTile - 1) / kSortTile + 1;
+    ws->level_tiles_max = (ws->node_cap + kLevelThreads - 1) / kLevelThreads + 1;
+    ws->groups_max = (n_max + 15) / 16 + 1;
+    const size_t v4 = p->precision == TREE_F64 ? sizeof(double4a) : sizeof(float4);
+    const size_t v2 = p->precision == TREE_F64 ? sizeof(double2a) : sizeof(float2);
+    bool ok = dalloc(&ws->key, N) && dalloc(&ws->key_alt, N) && dalloc(&ws->idx, N) && dalloc(&ws->idx_alt, N) &&
+              dalloc(&ws->hist, 2 * kSortPasses * kRadix) &&
+              dalloc(&ws->sort_status, (size_t)kSortPasses * ws->sort_tiles_max * kRadix) &&
+              dalloc(&ws->level_status, (size_t)kLevels * ws->level_tiles_max) && dalloc(&ws->ctr, kCtrCount) &&
+              dalloc(&ws->part, (size_t)kMaxBlocksReduce * 8) && dalloc(&ws->box, 1) &&
+              dalloc((unsigned char **)&ws->spos, N * v4) && dalloc(&ws->nfirst, NC) && dalloc(&ws->ncount, NC) &&
+              dalloc(&ws->ngeo, NC) && dalloc(&ws->nlink, NC) && dalloc(&ws->mom64, 10 * NC) &&
+              dalloc((unsigned char **)&ws->mom_a, NC * v4) && dalloc((unsigned char **)&ws->mom_b, NC * v4) &&
+              dalloc((unsigned char **)&ws->mom_c, NC * v2) && dalloc(&ws->dstatus, 1) &&
+              dalloc(&ws->stats, kStatCount) && dalloc(&ws->gstat, (size_t)ws->groups_max) &&
+              dalloc(&ws->dmac, kLevels);
+    if (!ok) {
+        free_all(ws);
+        delete ws;
+        cudaGetLastError();
+        return TREE_ERR_ALLOC;
+    }
+    if (cudaMemset(ws->dstatus, 0, sizeof(int32_t)) != cudaSuccess ||
+        cudaMemset(ws->stats, 0, kStatCount * sizeof(unsigned long long)) != cudaSuccess) {
+        free_all(ws);
+        delete ws;
+        return TREE_ERR_CUDA;
+    }
+    *out = ws;
+    return TREE_OK;
+}
+
+tree_status_t tree_workspace_destroy(TreeWorkspace *ws) {
+    if (!ws) return TREE_ERR_ARG;
+    cudaDeviceSynchronize();
+    free_all(ws);
+    delete ws;
+    return TREE_OK;
+}
+
+tree_status_t tree_set_params(TreeWorkspace *ws, const TreeParams *p) {
+    if (!ws) return TREE_ERR_ARG;
+    tree_status_t st = check_params(p);
+    if (st != TREE_OK) return st;
+    if (p->leaf_cap != ws->p.leaf_cap || p->precision != ws->p.precision) return TREE_ERR_ARG;
+    const bool regroup = p->group_size != ws->p.group_size;
+    const int64_t keep_cap = ws->p.node_cap;
+    ws->p = *p;
+    ws->p.node_cap = keep_cap;
+    if (regroup) ws->list_groups = -1;
+    return TREE_OK;
+}
+
+tree_status_t tree_get_params(const TreeWorkspace *ws, TreeParams *p) {
+    if (!ws || !p) return TREE_ERR_ARG;
+    *p = ws->p;
+    return TREE_OK;
+}
+
+tree_status_t tree_build(TreeWorkspace *ws, const void *x, int64_t n, int32_t dtype, void *stream) {
+    if (!ws) return TREE_ERR_ARG;
+    if (n < 0) return TREE_ERR_ARG;
+    if (n > ws->n_max) return TREE_ERR_CAPACITY;
+    if (dtype != ws->p.precision) return TREE_ERR_ARG;
+    if (n > 0 && !x) return TREE_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    ws->n = n;
+    ws->built = false;
+    ws->has_moments = false;
+    ws->list_groups = -1;
+    if (n == 0) { ws->built = true; return TREE_OK; }
+    const int64_t tiles = (n + kSortTile - 1) / kSortTile;
+    TRY_CUDA(cudaMemsetAsync(ws->ctr, 0, kCtrCount * sizeof(uint32_t), s));
+    TRY_CUDA(cudaMemsetAsync(ws->hist, 0, kSortPasses * kRadix * sizeof(uint32_t), s));
+    for (int p = 0; p < kSortPasses; ++p)
+        TRY_CUDA(cudaMemsetAsync(ws->sort_status + (size_t)p * ws->sort_tiles_max * kRadix, 0,
+                                 (size_t)tiles * kRadix * sizeof(uint32_t), s));
+    TRY_CUDA(cudaMemsetAsync(ws->level_status, 0, (size_t)kLevels * ws->level_tiles_max * sizeof(uint32_t), s));
+    {
+        PhaseScope ph(ws, TREE_PHASE_BOX, s);
+        TRY_CUDA(launch_box(ws, x, n, s));
+    }
+    {
+        PhaseScope ph(ws, TREE_PHASE_KEYS, s);
+        TRY_CUDA(launch_keys(ws, x, n, s));
+    }
+    {
+        PhaseScope ph(ws, TREE_PHASE_SORT, s);
+        TRY_CUDA(launch_sort(ws, n, s));
+    }
+    {
+        PhaseScope ph(ws, TREE_PHASE_OCTREE, s);
+        TRY_CUDA(launch_octree(ws, n, s));
+    }
+    ws->built = true;
+    return TREE_OK;
+}
+
+tree_status_t tree_moments(TreeWorkspace *ws, const void *x, const void *m, void *stream) {
+    if (!ws) return TREE_ERR_ARG;
+    if (!ws->built) return TREE_ERR_STATE;
+    if (ws->n == 0) { ws->has_moments = true; return TREE_OK; }
+    if (!x || !m) return TREE_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    {
+        PhaseScope ph(ws, TREE_PHASE_GATHER, s);
+        TRY_CUDA(launch_gather(ws, x, m, ws->n, s));
+    }
+    {
+        PhaseScope ph(ws, TREE_PHASE_MOMENTS, s);
+        TRY_CUDA(launch_moments(ws, s));
+    }
+    ws->has_moments = true;
+    return TREE_OK;
+}
+
+static tree_status_t walk(TreeWorkspace *ws, int mode, const WalkOut &out, cudaStream_t s) {
+    tree_status_t st = upload_mac(ws, s);
+    if (st != TREE_OK) return st;
+    PhaseScope ph(ws, mode == kWalkForce ? TREE_PHASE_WALK : TREE_PHASE_LISTS, s);
+    if (ws->p.precision == TREE_F64) TRY_CUDA(launch_walk_f64(ws, mode, out, s));
+    else TRY_CUDA(launch_walk_f32(ws, mode, out, s));
+    return TREE_OK;
+}
+
+static tree_status_t build_lists(TreeWorkspace *ws, cudaStream_t s) {
+    const int64_t ng = (ws->n + ws->p.group_size - 1) / ws->p.group_size;
+    WalkOut none{nullptr, nullptr, nullptr, 0.0};
+    tree_status_t st = walk(ws, kWalkCount, none, s);
+    if (st != TREE_OK) return st;
+    if (!ws->list_cnt && !dalloc(&ws->list_cnt, (size_t)(2 * (ws->groups_max + 1)))) return TREE_ERR_ALLOC;
+    {
+        PhaseScope ph(ws, TREE_PHASE_LISTS, s);
+        TRY_CUDA(launch_scan_lists(ws, ng, s));
+    }
+    int64_t tot[2];
+    TRY_CUDA(cudaMemcpyAsync(&tot[0], ws->list_cnt + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaMemcpyAsync(&tot[1], ws->list_cnt + (ng + 1) + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    if (tot[0] > ws->list_pc_cap) {
+        if (ws->pc_list) cudaFree(ws->pc_list);
+        ws->pc_list = nullptr;
+        ws->list_pc_cap = 0;
+        if (!dalloc(&ws->pc_list, (size_t)tot[0])) return TREE_ERR_ALLOC;
+        ws->list_pc_cap = tot[0];
+    }
+    if (tot[1] > ws->list_pp_cap) {
+        if (ws->pp_list) cudaFree(ws->pp_list);
+        ws->pp_list = nullptr;
+        ws->list_pp_cap = 0;
+        if (!dalloc(&ws->pp_list, (size_t)tot[1])) return TREE_ERR_ALLOC;
+        ws->list_pp_cap = tot[1];
+    }
+    st = walk(ws, kWalkEmit, none, s);
+    if (st != TREE_OK) return st;
+    ws->list_pc = tot[0];
+    ws->list_pp = tot[1];
+    ws->list_groups = ng;
+    return TREE_OK;
+}
+
+tree_status_t tree_forces(TreeWorkspace *ws, void *a, void *phi, int32_t flags, void *stream) {
+    if (!ws) return TREE_ERR_ARG;
+    if (!ws->has_moments) return TREE_ERR_STATE;
+    if (ws->n == 0) return TREE_OK;
+    if (!a) return TREE_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    if (flags & TREE_FLAG_EMIT_LISTS) {
+        tree_status_t st = build_lists(ws, s);
+        if (st != TREE_OK) return st;
+    }
+    WalkOut out{a, phi, nullptr, 0.0};
+    return walk(ws, kWalkForce, out, s);
+}
+
+tree_status_t tree_accel(TreeWorkspace *ws, const void *x, const void *m, int64_t n, void *a, void *phi,
+                         void *stream) {
+    if (!ws) return TREE_ERR_ARG;
+    if (n > 0 && (!x || !m || !a)) return TREE_ERR_ARG;
+    tree_status_t st = tree_build(ws, x, n, ws->p.precision, stream);
+    if (st != TREE_OK) return st;
+    st = tree_moments(ws, x, m, stream);
+    if (st != TREE_OK) return st;
+    return tree_forces(ws, a, phi, 0, stream);
+}
+
+tree_status_t leapfrog_step(TreeWorkspace *ws, void *x, void *v, const void *m, void *a, void *phi, double tau,
+                            int64_t n, void *stream) {
+    if (!ws) return TREE_ERR_ARG;
+    if (n < 0 || !isfinite(tau)) return TREE_ERR_ARG;
+    if (n > ws->n_max) return TREE_ERR_CAPACITY;
+    if (n == 0) return TREE_OK;
+    if (!x || !v || !m || !a) return TREE_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    ws->n = n;
+    ws->built = false;
+    ws->has_moments = false;
+    ws->list_groups = -1;
+    const int64_t tiles = (n + kSortTile - 1) / kSortTile;
+    TRY_CUDA(cudaMemsetAsync(ws->ctr, 0, kCtrCount * sizeof(uint32_t), s));
+    TRY_CUDA(cudaMemsetAsync(ws->hist, 0, kSortPasses * kRadix * sizeof(uint32_t), s));
+    for (int p = 0; p < kSortPasses; ++p)
+        TRY_CUDA(cudaMemsetAsync(ws->sort_status + (size_t)p * ws->sort_tiles_max * kRadix, 0,
+                                 (size_t)tiles * kRadix * sizeof(uint32_t), s));
+    TRY_CUDA(cudaMemsetAsync(ws->level_status, 0, (size_t)kLevels * ws->level_tiles_max * sizeof(uint32_t), s));
+    // Eqs. 2-3 fused with the box of the new positions
+    {
+        PhaseScope ph(ws, TREE_PHASE_BOX, s);
+        TRY_CUDA(launch_kick_drift_box(ws, x, v, a, tau, n, s));
+    }
+    // Eq. 4: tree at r^{n+1}
+    {
+        PhaseScope ph(ws, TREE_PHASE_KEYS, s);
+        TRY_CUDA(launch_keys(ws, x, n, s));
+    }
+    {
+        PhaseScope ph(ws, TREE_PHASE_SORT, s);
+        TRY_CUDA(launch_sort(ws, n, s));
+    }
+    {
+        PhaseScope ph(ws, TREE_PHASE_OCTREE, s);
+        TRY_CUDA(launch_octree(ws, n, s));
+    }
+    ws->built = true;
+    {
+        PhaseScope ph(ws, TREE_PHASE_GATHER, s);
+        TRY_CUDA(launch_gather(ws, x, m, n, s));
+    }
+    {
+        PhaseScope ph(ws, TREE_PHASE_MOMENTS, s);
+        TRY_CUDA(launch_moments(ws, s));
+    }
+    ws->has_moments = true;
+    // forces written back with the Eq. 5 kick fused in
+    WalkOut out{a, phi, v, 0.5 * tau};
+    return walk(ws, kWalkForce, out, s);
+}
+
+tree_status_t tree_diagnostics(TreeWorkspace *ws, const void *x, const void *v, const void *m, const void *phi,
+                               int64_t n, double *out, void *stream) {
+    if (!ws || !out || n < 0) return TREE_ERR_ARG;
+    if (n > 0 && (!x || !v || !m)) return TREE_ERR_ARG;
+    PhaseScope ph(ws, TREE_PHASE_DIAG, as_stream(stream));
+    TRY_CUDA(launch_diagnostics(ws, x, v, m, phi, n, out, as_stream(stream)));
+    return TREE_OK;
+}
+
+tree_status_t tree_direct_forces(TreeWorkspace *ws, const void *x, const void *m, int64_t n, int32_t dtype,
+                                 const int64_t *targets, int64_t nt, double *a_out, double *phi_out, void *stream) {
+    if (!ws || n < 0 || nt < 0) return TREE_ERR_ARG;
+    if (dtype != TREE_F32 && dtype != TREE_F64) return TREE_ERR_ARG;
+    if (nt == 0) return TREE_OK;
+    if (!x || !m || !targets || !a_out || n < 1) return TREE_ERR_ARG;
+    PhaseScope ph(ws, TREE_PHASE_DIRECT, as_stream(stream));
+    TRY_CUDA(launch_direct(ws, x, m, n, dtype, targets, nt, a_out, phi_out, as_stream(stream)));
+    return TREE_OK;
+}
+
+tree_status_t tree_timing_enable(TreeWorkspace *ws, int32_t enable) {
+    if (!ws) return TREE_ERR_ARG;
+    ws->timing = enable != 0;
+    if (ws->timing) {
+        ws->ev_used = 0;
+        ws->timed_launches = 0;
+    }
+    return TREE_OK;
+}
+
+tree_status_t tree_timing_read(TreeWorkspace *ws, double *ms, int64_t *calls, int64_t *launches) {
+    if (!ws || !ms) return TREE_ERR_ARG;
+    TRY_CUDA(cudaDeviceSynchronize());
+    for (int i = 0; i < TREE_NPHASES; ++i) {
+        ms[i] = 0.0;
+        if (calls) calls[i] = 0;
+    }
+    for (size_t k = 0; k < ws->ev_used; ++k) {
+        float t = 0.f;
+        TRY_CUDA(cudaEventElapsedTime(&t, ws->ev[2 * k], ws->ev[2 * k + 1]));
+        const int ph = ws->ev_phase[k];
+        ms[ph] += t;
+        if (calls) calls[ph] += 1;
+    }
+    if (launches) *launches = ws->timed_launches;
+    return TREE_OK;
+}
+
+tree_status_t tree_get_status(TreeWorkspace *ws, int32_t *status, int32_t clear) {
+    if (!ws || !status) return TREE_ERR_ARG;
+    TRY_CUDA(cudaDeviceSynchronize());
+    TRY_CUDA(cudaMemcpy(status, ws->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (clear) TRY_CUDA(cudaMemset(ws->dstatus, 0, sizeof(int32_t)));
+    return *status ? TREE_ERR_DEVICE : TREE_OK;
+}
+
+tree_status_t tree_get_info(TreeWorkspace *ws, TreeInfo *info) {
+    if (!ws || !info) return TREE_ERR_ARG;
+    memset(info, 0, sizeof(*info));
+    TRY_CUDA(cudaDeviceSynchronize());
+    info->n = ws->n;
+    info->n_groups = ws->n > 0 ? (ws->n + ws->p.group_size - 1) / ws->p.group_size : 0;
+    info->list_pc = ws->list_groups >= 0 ? ws->list_pc : 0;
+    info->list_pp = ws->list_groups >= 0 ? ws->list_pp : 0;
+    info->launches = ws->launches;
+    if (!ws->built || ws->n == 0) return TREE_OK;
+    uint32_t ctr[kCtrCount];
+    DevBox box;
+    TRY_CUDA(cudaMemcpy(ctr, ws->ctr, sizeof(ctr), cudaMemcpyDeviceToHost));
+    TRY_CUDA(cudaMemcpy(&box, ws->box, sizeof(box), cudaMemcpyDeviceToHost));
+    for (int l = 0; l <= kLevels; ++l) info->level_offset[l] = ctr[kCtrLevelStart + l];
+    info->n_nodes = info->level_offset[kLevels];
+    info->depth = 0;
+    for (int l = 0; l < kLevels; ++l)
+        if (info->level_offset[l + 1] > info->level_offset[l]) info->depth = l;
+    info->box_k = box.k;
+    for (int d = 0; d < 3; ++d) info->box_lo[d] = box.lo[d];
+    if (ws->has_moments) {
+        TRY_CUDA(launch_gstat_reduce(ws, info->n_groups, 0));
+        unsigned long long st[kStatCount];
+        TRY_CUDA(cudaMemcpy(st, ws->stats, sizeof(st), cudaMemcpyDeviceToHost));
+        info->pp_pairs = (int64_t)st[kStatPP];
+        info->pc_pairs = (int64_t)st[kStatPC];
+        info->max_stack = (int64_t)st[kStatMaxStack];
+    }
+    return TREE_OK;
+}
+
+tree_status_t tree_export_tree(TreeWorkspace *ws, uint64_t *keys, uint32_t *perm, int32_t *level, uint32_t *corner,
+                               uint32_t *first, uint32_t *count, int32_t *child, int32_t *nchild, void *stream) {
+    if (!ws) return TREE_ERR_ARG;
+    if (!ws->built) return TREE_ERR_STATE;
+    TreeInfo info;
+    tree_status_t st = tree_get_info(ws, &info);
+    if (st != TREE_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    const size_t n = (size_t)ws->n;
+    if (keys && n) TRY_CUDA(cudaMemcpyAsync(keys, ws->key, n * 8, cudaMemcpyDeviceToDevice, s));
+    if (perm && n) TRY_CUDA(cudaMemcpyAsync(perm, ws->idx, n * 4, cudaMemcpyDeviceToDevice, s));
+    TRY_CUDA(launch_export_tree(ws, info.n_nodes, level, corner, first, count, child, nchild, s));
+    return TREE_OK;
+}
+
+tree_status_t tree_export_moments(TreeWorkspace *ws, double *M, double *R, double *Q, void *stream) {
+    if (!ws) return TREE_ERR_ARG;
+    if (!ws->has_moments) return TREE_ERR_STATE;
+    TreeInfo info;
+    tree_status_t st = tree_get_info(ws, &info);
+    if (st != TREE_OK) return st;
+    const size_t nn = (size_t)info.n_nodes, cap = (size_t)ws->node_cap;
+    cudaStream_t s = as_stream(stream);
+    if (nn == 0) return TREE_OK;
+    if (M) TRY_CUDA(cudaMemcpyAsync(M, ws->mom64, nn * 8, cudaMemcpyDeviceToDevice, s));
+    for (int d = 0; d < 3; ++d)
+        if (R) TRY_CUDA(cudaMemcpyAsync(R + d * nn, ws->mom64 + (1 + d) * cap, nn * 8, cudaMemcpyDeviceToDevice, s));
+    for (int c = 0; c < 6; ++c)
+        if (Q) TRY_CUDA(cudaMemcpyAsync(Q + c * nn, ws->mom64 + (4 + c) * cap, nn * 8, cudaMemcpyDeviceToDevice, s));
+    return TREE_OK;
+}
+
+tree_status_t tree_export_lists(TreeWorkspace *ws, int64_t *pc_off, int32_t *pc_list, int64_t *pp_off,
+                                int32_t *pp_list, void *stream) {
+    if (!ws) return TREE_ERR_ARG;
+    if (ws->list_groups < 0) return TREE_ERR_STATE;
+    cudaStream_t s = as_stream(stream);
+    const size_t ng = (size_t)ws->list_groups;
+    if (pc_off) TRY_CUDA(cudaMemcpyAsync(pc_off, ws->list_cnt, (ng + 1) * 8, cudaMemcpyDeviceToDevice, s));
+    if (pp_off) TRY_CUDA(cudaMemcpyAsync(pp_off, ws->list_cnt + ng + 1, (ng + 1) * 8, cudaMemcpyDeviceToDevice, s));
+    if (pc_list && ws->list_pc)
+        TRY_CUDA(cudaMemcpyAsync(pc_list, ws->pc_list, (size_t)ws->list_pc * 4, cudaMemcpyDeviceToDevice, s));
+    if (pp_list && ws->list_pp)
+        TRY_CUDA(cudaMemcpyAsync(pp_list, ws->pp_list, (size_t)ws->list_pp * 4, cudaMemcpyDeviceToDevice, s));
+    return TREE_OK;
+}
+
+}  // extern "C"

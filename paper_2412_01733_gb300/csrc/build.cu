@@ -1,0 +1,503 @@
+// build.cu -- canonical tree construction on the GPU (Sec. 2 octree):
+//   box reduction (FP64), 63-bit Morton keys with the radix histograms of all
+//   eight sort passes fused in, stable onesweep LSD radix sort of
+//   (key, index), breadth-first octree built level by level with a
+//   decoupled look-back scan, and the gather of positions/masses into key
+//   order.
+#include <float.h>
+#include <math.h>
+
+#include "common.cuh"
+
+namespace treegb {
+
+// ============================================================== box reduction
+// Per-block FP64 min/max of the three coordinates; non-finite values set
+// TREE_DEV_NONFINITE and are left out of the box.
+template <typename Real>
+__global__ void __launch_bounds__(256) k_box_partial(const Real *__restrict__ x, int64_t n,
+                                                     double *__restrict__ part, int32_t *dstatus) {
+    __shared__ double sh[6][8];
+    double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double v = (double)x[d * n + i];
+            if (!isfinite(v)) { bad = true; continue; }
+            mn[d] = fmin(mn[d], v);
+            mx[d] = fmax(mx[d], v);
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_status(dstatus, TREE_DEV_NONFINITE);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+            mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        for (int d = 0; d < 3; ++d) { sh[d][warp] = mn[d]; sh[3 + d][warp] = mx[d]; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int c = threadIdx.x;
+        double r = sh[c][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = c < 3 ? fmin(r, sh[c][w]) : fmax(r, sh[c][w]);
+        part[blockIdx.x * 8 + c] = r;
+    }
+}
+
+// lo = min, ext = max_d (hi_d - lo_d) in FP64, L = 2^k the smallest power of
+// two strictly greater than ext (k = 0 when ext = 0): with ext = f 2^e,
+// f in [0.5, 1), that power is 2^e.
+__global__ void k_box_final(const double *__restrict__ part, int nblocks, DevBox *box) {
+    if (threadIdx.x != 0) return;
+    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int b = 0; b < nblocks; ++b) {
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = fmin(lo[d], part[b * 8 + d]);
+            hi[d] = fmax(hi[d], part[b * 8 + 3 + d]);
+        }
+    }
+    double ext = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        if (!(lo[d] <= hi[d])) { lo[d] = 0.0; hi[d] = 0.0; }  // no finite value on this axis
+        double e = __dsub_rn(hi[d], lo[d]);
+        if (e > ext) ext = e;
+    }
+    int k = 0;
+    if (ext > 0.0) frexp(ext, &k);
+    for (int d = 0; d < 3; ++d) box->lo[d] = lo[d];
+    box->k = k;
+    box->scale = ldexp(1.0, kBits - k);
+    box->unit = ldexp(1.0, k - kBits);
+}
+
+cudaError_t launch_box_final(TreeWorkspace *ws, int nblocks, cudaStream_t s) {
+    k_box_final<<<1, 32, 0, s>>>(ws->part, nblocks, ws->box);
+    ws->launches += 1;
+    return cudaGetLastError();
+}
+
+template <typename Real>
+static cudaError_t box_impl(TreeWorkspace *ws, const Real *x, int64_t n, cudaStream_t s) {
+    int nb = grid_for(n, 256, kMaxBlocksReduce);
+    k_box_partial<Real><<<nb, 256, 0, s>>>(x, n, ws->part, ws->dstatus);
+    ws->launches += 1;
+    return launch_box_final(ws, nb, s);
+}
+
+cudaError_t launch_box(TreeWorkspace *ws, const void *x, int64_t n, cudaStream_t s) {
+    if (ws->p.precision == TREE_F64) return box_impl(ws, (const double *)x, n, s);
+    return box_impl(ws, (const float *)x, n, s);
+}
+
+// ============================================================== keys + histograms
+// q_d = min(2^21-1, floor(fl(x_d - lo_d) * 2^(21-k))): the subtraction is the
+// only rounding (the scaling is by a power of two).  The key interleaves
+// q_x, q_y, q_z (x highest).  The same pass counts the eight 8-bit digits of
+// every key for the radix sort (warp-aggregated shared-memory atomics).
+template <typename Real>
+__global__ void __launch_bounds__(256) k_keys(const Real *__restrict__ x, int64_t n,
+                                              const DevBox *__restrict__ box,
+                                              uint64_t *__restrict__ key, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t sh[kSortPasses][kRadix];
+    for (int i = threadIdx.x; i < kSortPasses * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
+    __syncthreads();
+    const double lo0 = box->lo[0], lo1 = box->lo[1], lo2 = box->lo[2], scale = box->scale;
+    const double qmax = (double)((1u << kBits) - 1u);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t i = base + lane;
+        const bool valid = i < n;
+        uint64_t k = 0;
+        if (valid) {
+            double lo[3] = {lo0, lo1, lo2};
+            uint32_t q[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                double diff = __dsub_rn((double)x[d * n + i], lo[d]);
+                double f = floor(__dmul_rn(diff, scale));
+                if (!(f >= 0.0)) f = 0.0;  // also catches NaN
+                if (f > qmax) f = qmax;
+                q[d] = (uint32_t)f;
+            }
+            k = morton3(q[0], q[1], q[2]);
+            key[i] = k;
+        }
+#pragma unroll
+        for (int p = 0; p < kSortPasses; ++p) {
+            uint32_t dg = valid ? (uint32_t)((k >> (8 * p)) & 0xffu) : 0x100u;
+            uint32_t peers = __match_any_sync(0xffffffffu, dg);
+            if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&sh[p][dg], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSortPasses * kRadix; i += blockDim.x) {
+        uint32_t c = (&sh[0][0])[i];
+        if (c) atomicAdd(hist + i, c);
+    }
+}
+
+// Exclusive scan of each pass's 256 digit counts -> hist[2048 + p*256 + d].
+__global__ void __launch_bounds__(256) k_hist_scan(uint32_t *hist) {
+    __shared__ uint32_t wt[32];
+    const int p = blockIdx.x, d = threadIdx.x;
+    uint32_t c = hist[p * kRadix + d];
+    uint32_t e = block_exclusive_scan(c, wt, nullptr);
+    hist[kSortPasses * kRadix + p * kRadix + d] = e;
+}
+
+// ============================================================== onesweep pass
+// One block sorts one tile of kSortTile keys by the 8-bit digit at `shift`:
+// warp-level ranking with match_any (stable: a warp owns a contiguous
+// segment and walks it item by item, lanes in order), per-digit decoupled
+// look-back across tiles for the global position, then a scatter through
+// shared memory so that global writes are runs of equal digits.
+struct SortSmem {
+    uint64_t keys[kSortTile];
+    uint32_t vals[kSortTile];
+    uint32_t whist[kSortThreads / 32][kRadix];
+    uint32_t start[kRadix];
+    uint32_t gbase[kRadix];
+    uint32_t wt[32];
+    uint32_t tile;
+};
+
+template <bool FIRST>
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(
+    const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, int64_t n, int shift, const uint32_t *__restrict__ digit_off,
+    uint32_t *status, uint32_t *ticket, int32_t *dstatus) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SortSmem &S = *reinterpret_cast<SortSmem *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < (kSortThreads / 32) * kRadix; i += kSortThreads) (&S.whist[0][0])[i] = 0;
+    if (tid == 0) S.tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint32_t tile = S.tile;
+    const int64_t base = (int64_t)tile * kSortTile;
+
+    uint64_t k[kSortItems];
+    uint32_t v[kSortItems], dg[kSortItems], rk[kSortItems];
+    const int64_t wbase = base + warp * (kSortItems * 32);
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const int64_t pos = wbase + i * 32 + lane;
+        if (pos < n) {
+            k[i] = kin[pos];
+            v[i] = FIRST ? (uint32_t)pos : vin[pos];
+            dg[i] = (uint32_t)((k[i] >> shift) & 0xffu);
+        } else {
+            k[i] = 0; v[i] = 0; dg[i] = 0x100u;
+        }
+    }
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const uint32_t d = dg[i];
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t cnt = 0;
+        if (d < 0x100u) cnt = S.whist[warp][d];
+        __syncwarp();
+        const uint32_t pr = __popc(peers & lt);
+        if (d < 0x100u && pr == 0) S.whist[warp][d] = cnt + __popc(peers);
+        __syncwarp();
+        rk[i] = cnt + pr;
+    }
+    __syncthreads();
+    // thread t owns digit t: exclusive offsets over warps, tile count
+    uint32_t tcount = 0;
+    {
+        const int d = tid;
+#pragma unroll
+        for (int w = 0; w < kSortThreads / 32; ++w) {
+            uint32_t c = S.whist[w][d];
+            S.whist[w][d] = tcount;
+            tcount += c;
+        }
+    }
+    // per-digit look-back: status[tile * 256 + d]
+    {
+        const int d = tid;
+        uint32_t *st = status + d;  // word of digit d in tile t is st[t * 256]
+        uint32_t excl = 0;
+        if (tile == 0) {
+            st_release(st, kFlagInc | tcount);
+        } else {
+            st_release(st + (size_t)tile * kRadix, kFlagAgg | tcount);
+            int64_t p = (int64_t)tile - 1;
+            while (p >= 0) {
+                uint32_t w = ld_acquire(st + (size_t)p * kRadix);
+                if ((w & ~kValMask) == 0) {
+                    long long t0 = clock64();
+                    while (((w = ld_acquire(st + (size_t)p * kRadix)) & ~kValMask) == 0) {
+                        if (clock64() - t0 > kWaitCycles) {
+                            set_status(dstatus, TREE_DEV_TIMEOUT);
+                            w = kFlagInc;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                }
+                excl += w & kValMask;
+                if ((w & ~kValMask) == kFlagInc) break;
+                --p;
+            }
+            st_release(st + (size_t)tile * kRadix, kFlagInc | ((excl + tcount) & kValMask));
+        }
+        S.gbase[d] = digit_off[d] + excl;
+    }
+    uint32_t st0 = block_exclusive_scan(tcount, S.wt, nullptr);
+    S.start[tid] = st0;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const uint32_t d = dg[i];
+        if (d < 0x100u) {
+            const uint32_t p = S.start[d] + S.whist[warp][d] + rk[i];
+            S.keys[p] = k[i];
+            S.vals[p] = v[i];
+        }
+    }
+    __syncthreads();
+    const int64_t rem = n - base;
+    const int valid = rem < kSortTile ? (int)rem : kSortTile;
+    for (int j = tid; j < valid; j += kSortThreads) {
+        const uint64_t kk = S.keys[j];
+        const uint32_t d = (uint32_t)((kk >> shift) & 0xffu);
+        const uint32_t o = S.gbase[d] + (uint32_t)j - S.start[d];
+        kout[o] = kk;
+        vout[o] = S.vals[j];
+    }
+}
+
+template <typename Real>
+static cudaError_t keys_impl(TreeWorkspace *ws, const Real *x, int64_t n, cudaStream_t s) {
+    int nb = grid_for(n, 256, 152 * 8);
+    k_keys<Real><<<nb, 256, 0, s>>>(x, n, ws->box, ws->key, ws->hist);
+    k_hist_scan<<<kSortPasses, kRadix, 0, s>>>(ws->hist);
+    ws->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keys(TreeWorkspace *ws, const void *x, int64_t n, cudaStream_t s) {
+    if (ws->p.precision == TREE_F64) return keys_impl(ws, (const double *)x, n, s);
+    return keys_impl(ws, (const float *)x, n, s);
+}
+
+cudaError_t launch_sort(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
+    const int64_t tiles = (n + kSortTile - 1) / kSortTile;
+    const size_t smem = sizeof(SortSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_onesweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_onesweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    uint64_t *kin = ws->key, *kout = ws->key_alt;
+    uint32_t *vin = ws->idx, *vout = ws->idx_alt;
+    for (int p = 0; p < kSortPasses; ++p) {
+        uint32_t *st = ws->sort_status + (size_t)p * ws->sort_tiles_max * kRadix;
+        const uint32_t *off = ws->hist + kSortPasses * kRadix + p * kRadix;
+        uint32_t *tk = ws->ctr + kCtrSortTicket + p;
+        if (p == 0)
+            k_onesweep<true><<<(unsigned)tiles, kSortThreads, smem, s>>>(kin, vin, kout, vout, n, 8 * p, off, st, tk, ws->dstatus);
+        else
+            k_onesweep<false><<<(unsigned)tiles, kSortThreads, smem, s>>>(kin, vin, kout, vout, n, 8 * p, off, st, tk, ws->dstatus);
+        uint64_t *tk_ = kin; kin = kout; kout = tk_;
+        uint32_t *tv_ = vin; vin = vout; vout = tv_;
+    }
+    ws->launches += kSortPasses;
+    // 8 passes: the sorted data is back in ws->key / ws->idx
+    return cudaGetLastError();
+}
+
+// ============================================================== octree
+__global__ void k_tree_init(uint32_t *ctr, uint32_t *nfirst, uint32_t *ncount, int64_t n) {
+    const int t = threadIdx.x;
+    if (t < kLevels + 1) {
+        ctr[kCtrLevelTrunc + t] = 0xffffffffu;
+        ctr[kCtrLevelRawEnd + t] = 0;
+        ctr[kCtrLevelStart + t] = 0;
+    }
+    __syncthreads();
+    if (t == 0) {
+        ctr[kCtrLevelStart + 0] = 0;
+        ctr[kCtrLevelRawEnd + 0] = n > 0 ? 1u : 0u;
+        nfirst[0] = 0;
+        ncount[0] = (uint32_t)n;
+    }
+}
+
+// First index in [lo, hi) whose octant digit at `shift` is >= o (keys in the
+// range share their higher digits, so the digit is non-decreasing).
+__device__ __forceinline__ uint32_t digit_lower_bound(const uint64_t *__restrict__ skey, uint32_t lo,
+                                                      uint32_t hi, int shift, uint32_t o) {
+    while (lo < hi) {
+        uint32_t mid = lo + ((hi - lo) >> 1);
+        if ((uint32_t)((skey[mid] >> shift) & 7u) < o) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Level L: every node decides leaf/internal; internal nodes find their
+// octant boundaries by binary search, a block scan plus a decoupled
+// look-back across tiles numbers the children breadth-first, and the
+// children's ranges are written for level L+1.
+__global__ void __launch_bounds__(kLevelThreads) k_level(
+    int L, const uint64_t *__restrict__ skey, uint32_t *__restrict__ nfirst, uint32_t *__restrict__ ncount,
+    uint4 *__restrict__ ngeo, uint2 *__restrict__ nlink, uint32_t *ctr, uint32_t *lstatus,
+    uint32_t lcap, uint32_t node_cap, int32_t *dstatus) {
+    __shared__ uint32_t s_tile, s_excl, s_total;
+    __shared__ uint32_t wt[32];
+    const uint32_t start = ctr[kCtrLevelStart + L];
+    const uint32_t raw = ctr[kCtrLevelRawEnd + L], tr = ctr[kCtrLevelTrunc + L];
+    const uint32_t end = raw < tr ? raw : tr;
+    const uint32_t nl = end > start ? end - start : 0;
+    const uint32_t ntiles = (nl + kLevelThreads - 1) / kLevelThreads;
+    const int tid = threadIdx.x;
+    if (blockIdx.x == 0 && tid == 0) {
+        ctr[kCtrLevelStart + L + 1] = end;
+        if (ntiles == 0) ctr[kCtrLevelRawEnd + L + 1] = end;
+    }
+    const int shift = 3 * (kMaxLevel - 1 - L);
+    const uint32_t cmask = ~((1u << (kBits - L)) - 1u);
+    while (true) {
+        if (tid == 0) s_tile = atomicAdd(ctr + kCtrLevelTicket + L, 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        __syncthreads();
+        if (tile >= ntiles) break;
+        const uint32_t node = start + tile * kLevelThreads + tid;
+        const bool valid = node < end;
+        uint32_t first = 0, count = 0;
+        uint64_t k0 = 0;
+        if (valid) {
+            first = nfirst[node];
+            count = ncount[node];
+            k0 = skey[first];
+        }
+        bool internal = valid && count > lcap && L < kMaxLevel;
+        uint32_t b[9];
+        uint32_t nch = 0;
+        if (internal) {
+            const uint32_t e = first + count;
+            b[0] = first;
+            b[8] = e;
+#pragma unroll
+            for (int o = 1; o < 8; ++o) b[o] = digit_lower_bound(skey, b[o - 1], e, shift, (uint32_t)o);
+#pragma unroll
+            for (int o = 0; o < 8; ++o) nch += b[o + 1] > b[o] ? 1u : 0u;
+        }
+        uint32_t tot;
+        const uint32_t loc = block_exclusive_scan(nch, wt, &tot);
+        if (tid == 0) {
+            s_excl = lookback_single(lstatus, tile, tot, dstatus);
+            s_total = tot;
+        }
+        __syncthreads();
+        const uint32_t cf = end + s_excl + loc;
+        if (internal && (uint64_t)cf + nch > node_cap) {
+            internal = false;
+            atomicMin(ctr + kCtrLevelTrunc + L + 1, cf);
+            set_status(dstatus, TREE_DEV_NODES);
+        }
+        if (valid) {
+            const uint32_t cx = compact3(k0 >> 2) & cmask, cy = compact3(k0 >> 1) & cmask,
+                           cz = compact3(k0) & cmask;
+            ngeo[node] = make_uint4(cx, cy, cz, (uint32_t)L | (internal ? 0u : 0x100u));
+            nlink[node] = internal ? make_uint2(cf, nch) : make_uint2(first, count);
+        }
+        if (internal) {
+            uint32_t c = cf;
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                if (b[o + 1] > b[o]) {
+                    nfirst[c] = b[o];
+                    ncount[c] = b[o + 1] - b[o];
+                    ++c;
+                }
+            }
+        }
+        if (tile == ntiles - 1 && tid == 0) ctr[kCtrLevelRawEnd + L + 1] = end + s_excl + s_total;
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_octree(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
+    k_tree_init<<<1, 32, 0, s>>>(ws->ctr, ws->nfirst, ws->ncount, n);
+    double maxl = 1.0;
+    for (int L = 0; L < kLevels; ++L) {
+        double bound = fmin(fmin(maxl, (double)n), (double)ws->node_cap);
+        int nb = grid_for((int64_t)bound, kLevelThreads, 152 * 8);
+        uint32_t *lst = ws->level_status + (size_t)L * ws->level_tiles_max;
+        k_level<<<nb, kLevelThreads, 0, s>>>(L, ws->key, ws->nfirst, ws->ncount, ws->ngeo, ws->nlink,
+                                             ws->ctr, lst, (uint32_t)ws->p.leaf_cap,
+                                             (uint32_t)ws->node_cap, ws->dstatus);
+        maxl *= 8.0;
+    }
+    ws->launches += 1 + kLevels;
+    return cudaGetLastError();
+}
+
+// ============================================================== gather
+template <typename Real>
+__global__ void __launch_bounds__(256) k_gather(const Real *__restrict__ x, const Real *__restrict__ m,
+                                                const uint32_t *__restrict__ idx, int64_t n,
+                                                typename Vec4<Real>::T *__restrict__ spos) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = idx[s];
+        typename Vec4<Real>::T p;
+        p.x = x[i];
+        p.y = x[n + i];
+        p.z = x[2 * n + i];
+        p.w = m[i];
+        spos[s] = p;
+    }
+}
+
+cudaError_t launch_gather(TreeWorkspace *ws, const void *x, const void *m, int64_t n, cudaStream_t s) {
+    int nb = grid_for(n, 256, 152 * 16);
+    if (ws->p.precision == TREE_F64)
+        k_gather<double><<<nb, 256, 0, s>>>((const double *)x, (const double *)m, ws->idx, n,
+                                            (double4a *)ws->spos);
+    else
+        k_gather<float><<<nb, 256, 0, s>>>((const float *)x, (const float *)m, ws->idx, n,
+                                           (float4 *)ws->spos);
+    ws->launches += 1;
+    return cudaGetLastError();
+}
+
+// ============================================================== export (tests)
+__global__ void k_export_tree(const uint4 *__restrict__ ngeo, const uint2 *__restrict__ nlink,
+                              const uint32_t *__restrict__ nfirst, const uint32_t *__restrict__ ncount,
+                              int64_t nn, int32_t *level, uint32_t *corner, uint32_t *first, uint32_t *count,
+                              int32_t *child, int32_t *nchild) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nn; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 g = ngeo[c];
+        const uint2 l = nlink[c];
+        const bool leaf = (g.w >> 8) & 1u;
+        if (level) level[c] = (int32_t)(g.w & 0xffu);
+        if (corner) { corner[c] = g.x; corner[nn + c] = g.y; corner[2 * nn + c] = g.z; }
+        if (first) first[c] = nfirst[c];
+        if (count) count[c] = ncount[c];
+        if (child) child[c] = leaf ? -1 : (int32_t)l.x;
+        if (nchild) nchild[c] = leaf ? 0 : (int32_t)l.y;
+    }
+}
+
+cudaError_t launch_export_tree(TreeWorkspace *ws, int64_t nn, int32_t *level, uint32_t *corner, uint32_t *first,
+                               uint32_t *count, int32_t *child, int32_t *nchild, cudaStream_t s) {
+    if (nn <= 0) return cudaSuccess;
+    k_export_tree<<<grid_for(nn, 256, 152 * 8), 256, 0, s>>>(ws->ngeo, ws->nlink, ws->nfirst, ws->ncount, nn,
+                                                              level, corner, first, count, child, nchild);
+    ws->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace treegb

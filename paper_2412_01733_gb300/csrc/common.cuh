@@ -1,0 +1,279 @@
+// common.cuh -- internal definitions shared by the treegb CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/treegb.h"
+
+namespace treegb {
+
+constexpr int kBits = 21;          // bits per axis of the quantised coordinates
+constexpr int kMaxLevel = 21;      // deepest octree level
+constexpr int kLevels = 22;        // levels 0..21
+constexpr int kSortThreads = 256;  // onesweep block
+constexpr int kSortItems = 16;     // keys per thread
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSortPasses = 8;     // 8-bit digits over the 64-bit key
+constexpr int kRadix = 256;
+constexpr int kLevelThreads = 256;  // octree level block (nodes per tile)
+constexpr int kMaxBlocksReduce = 1024;  // partial-result slots of the reductions
+constexpr int kMaxLeafSmall = 16;   // leaves up to this size are expanded in the walk buffer
+constexpr int64_t kMaxNodes = (int64_t)1 << 29;  // node indices fit 29 bits (walk stack entries)
+
+// lookback status words: 2-bit flag + 30-bit value
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1u;
+// bounded waits: give up after this many clock cycles (about 1 s)
+constexpr long long kWaitCycles = 2000000000LL;
+
+struct __align__(32) double4a { double x, y, z, w; };
+struct __align__(16) double2a { double x, y; };
+
+template <typename Real> struct Vec4;
+template <> struct Vec4<float> { using T = float4; };
+template <> struct Vec4<double> { using T = double4a; };
+template <typename Real> struct Vec2;
+template <> struct Vec2<float> { using T = float2; };
+template <> struct Vec2<double> { using T = double2a; };
+
+// Box of the last build, written by the device.
+struct DevBox {
+    double lo[3];
+    double scale;   // 2^(21-k)
+    double unit;    // 2^(k-21): grid spacing
+    int32_t k;
+    int32_t pad;
+};
+
+// Offsets into the counter block (uint32), cleared at the start of a build.
+// Level l holds nodes [lvl_start[l], lvl_start[l+1]).  While the octree is
+// built, level l's end is min(raw_end[l], trunc[l]): raw_end is the child
+// total of level l-1, trunc the first child slot of a parent that was turned
+// into a leaf because the node array was full.
+enum CounterSlots {
+    kCtrSortTicket = 0,                       // 8 tickets
+    kCtrLevelTicket = kCtrSortTicket + 8,     // 22 tickets
+    kCtrLevelStart = kCtrLevelTicket + 24,    // 23 level starts
+    kCtrLevelRawEnd = kCtrLevelStart + 24,    // 23 raw ends
+    kCtrLevelTrunc = kCtrLevelRawEnd + 24,    // 23 truncation points
+    kCtrCount = kCtrLevelTrunc + 24
+};
+
+// Statistics slots (unsigned long long), cleared at the start of each walk.
+enum StatSlots { kStatPP = 0, kStatPC = 1, kStatMaxStack = 2, kStatCount = 8 };
+
+}  // namespace treegb
+
+// Opaque to C callers.
+struct TreeWorkspace {
+    int device = 0;
+    int64_t n_max = 0;
+    int64_t n = 0;
+    TreeParams p{};
+    int64_t node_cap = 0;
+    int64_t sort_tiles_max = 0;
+    int64_t level_tiles_max = 0;
+    size_t real_size = 4;
+
+    // sort
+    uint64_t *key = nullptr, *key_alt = nullptr;
+    uint32_t *idx = nullptr, *idx_alt = nullptr;
+    uint32_t *hist = nullptr;          // [8][256] counts, then exclusive offsets
+    uint32_t *sort_status = nullptr;   // [8][tiles][256]
+    uint32_t *level_status = nullptr;  // [22][level_tiles]
+    uint32_t *ctr = nullptr;           // kCtrCount words
+    // box
+    double *part = nullptr;            // reduction partials [kMaxBlocksReduce][8]
+    treegb::DevBox *box = nullptr;
+    // sorted particles (float4 / double4a)
+    void *spos = nullptr;
+    // nodes
+    uint32_t *nfirst = nullptr, *ncount = nullptr;
+    uint4 *ngeo = nullptr;             // {cx, cy, cz, level | leaf << 8}
+    uint2 *nlink = nullptr;            // internal: {child, nchild}; leaf: {first, count}
+    double *mom64 = nullptr;           // [10][node_cap]: M, Rx, Ry, Rz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz
+    void *mom_a = nullptr;             // Vec4: (Rx, Ry, Rz, M)
+    void *mom_b = nullptr;             // Vec4: (Qxx, Qyy, Qzz, Qxy)
+    void *mom_c = nullptr;             // Vec2: (Qxz, Qyz)
+    // status and statistics
+    int32_t *dstatus = nullptr;
+    unsigned long long *stats = nullptr;
+    uint4 *gstat = nullptr;            // per walk group: {n_pc, n_pp particles, max stack, n_pp leaves}
+    int64_t groups_max = 0;
+    // interaction lists (allocated on first use)
+    int64_t *list_cnt = nullptr;       // [2][groups+1] counts -> offsets
+    int32_t *pc_list = nullptr, *pp_list = nullptr;
+    int64_t list_pc_cap = 0, list_pp_cap = 0, list_pc = 0, list_pp = 0;
+    int64_t list_groups = -1;
+    // direct-sum scratch
+    double *direct_part = nullptr;
+    size_t direct_part_bytes = 0;
+    // host-side state
+    int64_t mac_D[treegb::kLevels];
+    double mac_theta = -1.0;
+    int64_t *dmac = nullptr;           // device copy of mac_D
+    bool built = false, has_moments = false;
+    // kernel launch count and optional per-phase event timing
+    int64_t launches = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;       // pairs (start, stop)
+    std::vector<int> ev_phase;         // phase of each pair
+    size_t ev_used = 0;                // pairs recorded since the last read
+    int64_t timed_launches = 0;        // kernels launched inside timed phases
+};
+
+namespace treegb {
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Spread the low 21 bits of v so that bit b lands at bit 3b.
+__host__ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x1f00000000ffffULL;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffULL;
+    x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
+    x = (x | (x << 2)) & 0x1249249249249249ULL;
+    return x;
+}
+// Inverse of spread3: gather bits 3b into bit b.
+__host__ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
+    x &= 0x1249249249249249ULL;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ULL;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00fULL;
+    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffULL;
+    x = (x ^ (x >> 16)) & 0x1f00000000ffffULL;
+    x = (x ^ (x >> 32)) & 0x1fffffULL;
+    return (uint32_t)x;
+}
+__host__ __device__ __forceinline__ uint64_t morton3(uint32_t qx, uint32_t qy, uint32_t qz) {
+    return (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+}
+
+__device__ __forceinline__ void set_status(int32_t *st, int32_t bits) {
+    atomicOr(st, bits);
+}
+
+// Single-value decoupled look-back: returns the exclusive prefix of tile
+// `tile` given its aggregate.  Call from one thread.  A wait that exceeds
+// kWaitCycles sets TREE_DEV_TIMEOUT and ends the look-back (the published
+// inclusive value is then wrong, but every waiter terminates).
+__device__ inline uint32_t lookback_single(uint32_t *status, uint32_t tile, uint32_t agg,
+                                           int32_t *dstatus) {
+    if (tile == 0) {
+        st_release(status, kFlagInc | (agg & kValMask));
+        return 0;
+    }
+    st_release(status + tile, kFlagAgg | (agg & kValMask));
+    uint32_t excl = 0;
+    int64_t p = (int64_t)tile - 1;
+    while (p >= 0) {
+        uint32_t v = ld_acquire(status + p);
+        if ((v & ~kValMask) == 0) {
+            long long t0 = clock64();
+            while (((v = ld_acquire(status + p)) & ~kValMask) == 0) {
+                if (clock64() - t0 > kWaitCycles) {
+                    set_status(dstatus, TREE_DEV_TIMEOUT);
+                    v = kFlagInc;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        excl += v & kValMask;
+        if ((v & ~kValMask) == kFlagInc) break;
+        --p;
+    }
+    st_release(status + tile, kFlagInc | ((excl + agg) & kValMask));
+    return excl;
+}
+
+// Block-wide exclusive scan of one uint32 per thread (blockDim.x multiple of 32,
+// at most 1024 threads).  `warp_tot` is shared scratch of 32 words.
+__device__ inline uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_tot, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) warp_tot[lane] = t;  // inclusive over warps
+    }
+    __syncthreads();
+    uint32_t before = warp == 0 ? 0 : warp_tot[warp - 1];
+    if (total) *total = warp_tot[nw - 1];
+    uint32_t r = before + x - v;
+    __syncthreads();
+    return r;
+}
+
+inline int grid_for(int64_t n, int threads, int max_blocks) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (int)b;
+}
+
+}  // namespace treegb
+
+// ---------------------------------------------------------------- host-side entry points of each .cu
+namespace treegb {
+// build.cu
+cudaError_t launch_box(TreeWorkspace *ws, const void *x, int64_t n, cudaStream_t s);
+cudaError_t launch_box_final(TreeWorkspace *ws, int nblocks, cudaStream_t s);
+cudaError_t launch_keys(TreeWorkspace *ws, const void *x, int64_t n, cudaStream_t s);
+cudaError_t launch_sort(TreeWorkspace *ws, int64_t n, cudaStream_t s);
+cudaError_t launch_octree(TreeWorkspace *ws, int64_t n, cudaStream_t s);
+cudaError_t launch_gather(TreeWorkspace *ws, const void *x, const void *m, int64_t n, cudaStream_t s);
+cudaError_t launch_export_tree(TreeWorkspace *ws, int64_t nn, int32_t *level, uint32_t *corner, uint32_t *first,
+                               uint32_t *count, int32_t *child, int32_t *nchild, cudaStream_t s);
+// moments.cu
+cudaError_t launch_moments(TreeWorkspace *ws, cudaStream_t s);
+// walk_f32.cu / walk_f64.cu
+enum WalkMode { kWalkForce = 0, kWalkCount = 1, kWalkEmit = 2 };
+struct WalkOut {
+    void *a;            // [3][n] caller order (or NULL in count/emit modes)
+    void *phi;          // [n] or NULL
+    void *v;            // leapfrog: [3][n] velocities to kick, or NULL
+    double half_tau;    // leapfrog kick
+};
+cudaError_t launch_walk_f32(TreeWorkspace *ws, int mode, const WalkOut &out, cudaStream_t s);
+cudaError_t launch_walk_f64(TreeWorkspace *ws, int mode, const WalkOut &out, cudaStream_t s);
+// integrate.cu
+cudaError_t launch_kick_drift_box(TreeWorkspace *ws, void *x, void *v, const void *a, double tau,
+                                  int64_t n, cudaStream_t s);
+cudaError_t launch_diagnostics(TreeWorkspace *ws, const void *x, const void *v, const void *m,
+                               const void *phi, int64_t n, double *out, cudaStream_t s);
+cudaError_t launch_direct(TreeWorkspace *ws, const void *x, const void *m, int64_t n, int dtype,
+                          const int64_t *targets, int64_t nt, double *a_out, double *phi_out,
+                          cudaStream_t s);
+cudaError_t launch_scan_lists(TreeWorkspace *ws, int64_t ngroups, cudaStream_t s);
+cudaError_t launch_gstat_reduce(TreeWorkspace *ws, int64_t ngroups, cudaStream_t s);
+}  // namespace treegb

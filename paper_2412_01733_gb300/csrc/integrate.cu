@@ -1,0 +1,320 @@
+// integrate.cu -- leapfrog kick+drift fused with the box reduction (Eqs. 2-3),
+// FP64 diagnostics, the direct-summation reference of Eq. 1, and the small
+// scans/reductions over per-group walk records.
+#include <float.h>
+#include <math.h>
+
+#include "common.cuh"
+
+namespace treegb {
+
+// ============================================================== kick + drift + box
+// v += tau/2 a (Eq. 2); x += tau v (Eq. 3); per-block FP64 min/max of the new
+// positions for the next tree (the same partial layout as the box kernel).
+template <typename Real>
+__global__ void __launch_bounds__(256) k_kick_drift_box(Real *__restrict__ x, Real *__restrict__ v,
+                                                        const Real *__restrict__ a, Real half_tau, Real tau,
+                                                        int64_t n, double *__restrict__ part,
+                                                        int32_t *dstatus) {
+    __shared__ double sh[6][8];
+    double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const Real vv = fma(half_tau, a[d * n + i], v[d * n + i]);
+            const Real xx = fma(tau, vv, x[d * n + i]);
+            v[d * n + i] = vv;
+            x[d * n + i] = xx;
+            const double w = (double)xx;
+            if (!isfinite(w)) { bad = true; continue; }
+            mn[d] = fmin(mn[d], w);
+            mx[d] = fmax(mx[d], w);
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_status(dstatus, TREE_DEV_NONFINITE);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+            mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        for (int d = 0; d < 3; ++d) { sh[d][warp] = mn[d]; sh[3 + d][warp] = mx[d]; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int c = threadIdx.x;
+        double r = sh[c][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = c < 3 ? fmin(r, sh[c][w]) : fmax(r, sh[c][w]);
+        part[blockIdx.x * 8 + c] = r;
+    }
+}
+
+
+cudaError_t launch_kick_drift_box(TreeWorkspace *ws, void *x, void *v, const void *a, double tau,
+                                  int64_t n, cudaStream_t s) {
+    int nb = grid_for(n, 256, kMaxBlocksReduce);
+    if (ws->p.precision == TREE_F64)
+        k_kick_drift_box<double><<<nb, 256, 0, s>>>((double *)x, (double *)v, (const double *)a, 0.5 * tau,
+                                                    tau, n, ws->part, ws->dstatus);
+    else
+        k_kick_drift_box<float><<<nb, 256, 0, s>>>((float *)x, (float *)v, (const float *)a, (float)(0.5 * tau),
+                                                   (float)tau, n, ws->part, ws->dstatus);
+    ws->launches += 1;
+    return launch_box_final(ws, nb, s);
+}
+
+// ============================================================== diagnostics (FP64)
+// E_kin = 1/2 sum m v^2, W = 1/2 sum m phi, P = sum m v, L = sum m x cross v.
+// Fixed grid and fixed reduction order: deterministic.
+template <typename Real>
+__global__ void __launch_bounds__(256) k_diag_partial(const Real *__restrict__ x, const Real *__restrict__ v,
+                                                      const Real *__restrict__ m, const Real *__restrict__ phi,
+                                                      int64_t n, double *__restrict__ part) {
+    __shared__ double sh[8][8];
+    double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double mi = (double)m[i];
+        const double x0 = x[i], x1 = x[n + i], x2 = x[2 * n + i];
+        const double v0 = v[i], v1 = v[n + i], v2 = v[2 * n + i];
+        q[0] += 0.5 * mi * (v0 * v0 + v1 * v1 + v2 * v2);
+        if (phi) q[1] += 0.5 * mi * (double)phi[i];
+        q[2] += mi * v0; q[3] += mi * v1; q[4] += mi * v2;
+        q[5] += mi * (x1 * v2 - x2 * v1);
+        q[6] += mi * (x2 * v0 - x0 * v2);
+        q[7] += mi * (x0 * v1 - x1 * v0);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        for (int o = 16; o > 0; o >>= 1) q[c] += __shfl_xor_sync(0xffffffffu, q[c], o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int c = 0; c < 8; ++c) sh[c][warp] = q[c];
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double r = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[threadIdx.x][w];
+        part[blockIdx.x * 8 + threadIdx.x] = r;
+    }
+}
+
+__global__ void k_diag_final(const double *__restrict__ part, int nb, double *out) {
+    if (threadIdx.x < 8) {
+        double r = 0;
+        for (int b = 0; b < nb; ++b) r += part[b * 8 + threadIdx.x];
+        out[threadIdx.x] = r;
+    }
+}
+
+cudaError_t launch_diagnostics(TreeWorkspace *ws, const void *x, const void *v, const void *m,
+                               const void *phi, int64_t n, double *out, cudaStream_t s) {
+    int nb = grid_for(n, 256, kMaxBlocksReduce);
+    if (ws->p.precision == TREE_F64)
+        k_diag_partial<double><<<nb, 256, 0, s>>>((const double *)x, (const double *)v, (const double *)m,
+                                                  (const double *)phi, n, ws->part);
+    else
+        k_diag_partial<float><<<nb, 256, 0, s>>>((const float *)x, (const float *)v, (const float *)m,
+                                                 (const float *)phi, n, ws->part);
+    k_diag_final<<<1, 32, 0, s>>>(ws->part, nb, out);
+    ws->launches += 2;
+    return cudaGetLastError();
+}
+
+// ============================================================== direct sum (Eq. 1)
+// blockIdx.x: 128 targets; blockIdx.y: one chunk of sources.  FP32: pair terms
+// in FP32, per-128-source partial sums folded with Kahan compensation; the
+// chunk totals are written in FP64 and summed over chunks in a fixed order.
+constexpr int kDirThreads = 128;
+
+template <typename Real>
+__global__ void __launch_bounds__(kDirThreads) k_direct(const Real *__restrict__ x, const Real *__restrict__ m,
+                                                        int64_t n, const int64_t *__restrict__ tgt, int64_t nt,
+                                                        int64_t chunk, double eps2d, double *__restrict__ part) {
+    using V4 = typename Vec4<Real>::T;
+    __shared__ V4 src[kDirThreads];
+    const int64_t t = blockIdx.x * (int64_t)kDirThreads + threadIdx.x;
+    const int64_t ti = t < nt ? tgt[t] : -1;
+    Real px = 0, py = 0, pz = 0;
+    if (ti >= 0) { px = x[ti]; py = x[n + ti]; pz = x[2 * n + ti]; }
+    const Real eps2 = (Real)eps2d;
+    const int64_t j0 = blockIdx.y * chunk;
+    const int64_t j1 = min(n, j0 + chunk);
+    Real sum[4] = {0, 0, 0, 0}, cmp[4] = {0, 0, 0, 0};
+    for (int64_t jb = j0; jb < j1; jb += kDirThreads) {
+        const int64_t j = jb + threadIdx.x;
+        V4 s;
+        if (j < j1) { s.x = x[j]; s.y = x[n + j]; s.z = x[2 * n + j]; s.w = m[j]; }
+        else { s.x = s.y = s.z = s.w = 0; }
+        __syncthreads();
+        src[threadIdx.x] = s;
+        __syncthreads();
+        const int ns = (int)min((int64_t)kDirThreads, j1 - jb);
+        Real part_[4] = {0, 0, 0, 0};
+        for (int k = 0; k < ns; ++k) {
+            if (jb + k == ti) continue;
+            const V4 q = src[k];
+            const Real dx = q.x - px, dy = q.y - py, dz = q.z - pz;
+            const Real r2 = dx * dx + dy * dy + dz * dz + eps2;
+            if (!(r2 > Real(0))) continue;
+            const Real r = sqrt(r2);
+            const Real w = q.w / (r2 * r);
+            part_[0] += w * dx; part_[1] += w * dy; part_[2] += w * dz;
+            part_[3] -= q.w / r;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const Real y = part_[c] - cmp[c];
+            const Real tt = sum[c] + y;
+            cmp[c] = (tt - sum[c]) - y;
+            sum[c] = tt;
+        }
+    }
+    if (t < nt) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            part[((int64_t)blockIdx.y * 4 + c) * nt + t] = (double)sum[c] - (double)cmp[c];
+    }
+}
+
+__global__ void k_direct_final(const double *__restrict__ part, int64_t nt, int nchunks, double G,
+                               double *__restrict__ a_out, double *__restrict__ phi_out) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    double r[4] = {0, 0, 0, 0};
+    for (int c = 0; c < nchunks; ++c)
+        for (int k = 0; k < 4; ++k) r[k] += part[((int64_t)c * 4 + k) * nt + t];
+    a_out[t] = G * r[0];
+    a_out[nt + t] = G * r[1];
+    a_out[2 * nt + t] = G * r[2];
+    if (phi_out) phi_out[t] = G * r[3];
+}
+
+cudaError_t launch_direct(TreeWorkspace *ws, const void *x, const void *m, int64_t n, int dtype,
+                          const int64_t *targets, int64_t nt, double *a_out, double *phi_out,
+                          cudaStream_t s) {
+    const int64_t tt = (nt + kDirThreads - 1) / kDirThreads;
+    int64_t nch = (152 * 16 + tt - 1) / tt;
+    int64_t maxch = (n + kDirThreads - 1) / kDirThreads;
+    if (nch > maxch) nch = maxch;
+    if (nch < 1) nch = 1;
+    if (nch > 65535) nch = 65535;
+    int64_t chunk = (n + nch - 1) / nch;
+    chunk = ((chunk + kDirThreads - 1) / kDirThreads) * kDirThreads;
+    nch = (n + chunk - 1) / chunk;
+    if (nch < 1) nch = 1;
+    const size_t need = (size_t)nch * 4 * (size_t)nt * sizeof(double);
+    if (need > ws->direct_part_bytes) {
+        if (ws->direct_part) cudaFree(ws->direct_part);
+        ws->direct_part = nullptr;
+        ws->direct_part_bytes = 0;
+        cudaError_t e = cudaMalloc(&ws->direct_part, need);
+        if (e != cudaSuccess) return e;
+        ws->direct_part_bytes = need;
+    }
+    dim3 grid((unsigned)tt, (unsigned)nch);
+    const double eps2 = ws->p.eps * ws->p.eps;
+    if (dtype == TREE_F64)
+        k_direct<double><<<grid, kDirThreads, 0, s>>>((const double *)x, (const double *)m, n, targets, nt, chunk,
+                                                      eps2, ws->direct_part);
+    else
+        k_direct<float><<<grid, kDirThreads, 0, s>>>((const float *)x, (const float *)m, n, targets, nt, chunk,
+                                                     eps2, ws->direct_part);
+    k_direct_final<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(ws->direct_part, nt, (int)nch, ws->p.G, a_out,
+                                                                phi_out);
+    ws->launches += 2;
+    return cudaGetLastError();
+}
+
+// ============================================================== per-group walk records
+// gstat[g] = {n_pc cells, n_pp particles, max stack, n_pp leaves}.
+// Pair totals: sum_g |g| n_pc and sum_g |g| n_pp; deepest stack.
+__global__ void __launch_bounds__(256) k_gstat_reduce(const uint4 *__restrict__ gstat, int64_t ng, int64_t n,
+                                                      int gs, unsigned long long *stats) {
+    unsigned long long pp = 0, pc = 0, ms = 0;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 r = gstat[g];
+        const int64_t rem = n - g * gs;
+        const unsigned long long c = (unsigned long long)(rem < gs ? rem : gs);
+        pc += c * r.x;
+        pp += c * r.y;
+        ms = ms > r.z ? ms : r.z;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        pp += __shfl_xor_sync(0xffffffffu, pp, o);
+        pc += __shfl_xor_sync(0xffffffffu, pc, o);
+        unsigned long long t = __shfl_xor_sync(0xffffffffu, ms, o);
+        ms = ms > t ? ms : t;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(stats + kStatPP, pp);
+        atomicAdd(stats + kStatPC, pc);
+        atomicMax(stats + kStatMaxStack, ms);
+    }
+}
+
+// Exclusive scans of the per-group list lengths (x: PC cells, w: PP leaves)
+// into list_off[0..ng] and list_off[ng+1 .. 2ng+1].  Single block: the list
+// path is a test/adjoint path, not the force hot path.
+__global__ void __launch_bounds__(1024) k_list_scan(const uint4 *__restrict__ gstat, int64_t ng,
+                                                    int64_t *__restrict__ off) {
+    __shared__ unsigned long long wt[2][32];
+    __shared__ unsigned long long carry[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 2) carry[tid] = 0;
+    __syncthreads();
+    for (int64_t b = 0; b < ng; b += 1024) {
+        const int64_t g = b + tid;
+        unsigned long long v[2] = {0, 0};
+        if (g < ng) { const uint4 r = gstat[g]; v[0] = r.x; v[1] = r.w; }
+        unsigned long long x[2] = {v[0], v[1]};
+        for (int o = 1; o < 32; o <<= 1) {
+            for (int c = 0; c < 2; ++c) {
+                unsigned long long y = __shfl_up_sync(0xffffffffu, x[c], o);
+                if (lane >= o) x[c] += y;
+            }
+        }
+        if (lane == 31) { wt[0][warp] = x[0]; wt[1][warp] = x[1]; }
+        __syncthreads();
+        if (warp == 0) {
+            for (int c = 0; c < 2; ++c) {
+                unsigned long long t = wt[c][lane];
+                for (int o = 1; o < 32; o <<= 1) {
+                    unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+                    if (lane >= o) t += y;
+                }
+                wt[c][lane] = t;
+            }
+        }
+        __syncthreads();
+        for (int c = 0; c < 2; ++c) {
+            const unsigned long long before = (warp ? wt[c][warp - 1] : 0ull) + carry[c];
+            if (g < ng) off[c * (ng + 1) + g] = (int64_t)(before + x[c] - v[c]);
+        }
+        __syncthreads();
+        if (tid < 2) carry[tid] += wt[tid][31];
+        __syncthreads();
+    }
+    if (tid < 2) off[tid * (ng + 1) + ng] = (int64_t)carry[tid];
+}
+
+cudaError_t launch_scan_lists(TreeWorkspace *ws, int64_t ngroups, cudaStream_t s) {
+    k_list_scan<<<1, 1024, 0, s>>>(ws->gstat, ngroups, ws->list_cnt);
+    ws->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gstat_reduce(TreeWorkspace *ws, int64_t ngroups, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(ws->stats, 0, kStatCount * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_gstat_reduce<<<grid_for(ngroups, 256, 152 * 4), 256, 0, s>>>(ws->gstat, ngroups, ws->n, ws->p.group_size,
+                                                                    ws->stats);
+    ws->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace treegb

@@ -1,0 +1,500 @@
+// walk.cuh -- the tree walk and force evaluation (Sec. 2 TreeCode; Eq. 1 for
+// the near part), one warp per group of Gs key-ordered particles.
+//
+// Traversal (per warp, depth first, stack in shared memory):
+//   the stack holds ranges of sibling nodes (children are contiguous in the
+//   breadth-first numbering), one entry per opened cell.  Each step pops up
+//   to 32 nodes from the top ranges (splitting the last one if needed), one
+//   node per lane, and tests each against the group box with the integer
+//   opening criterion d2 >= D[level] (D from tree_mac_table): far nodes go
+//   to the PC buffer, near leaves' particles to the PP buffer, near internal
+//   nodes push their child range.  Compaction uses warp ballots and scans.
+// Evaluation: whenever a buffer holds 32 entries, the warp stages the 32
+//   sources (float4 position+mass, or the cell's mass, COM and quadrupole)
+//   in shared memory and every lane applies all 32 to its own target(s)
+//   (each source is a broadcast shared-memory read; the arithmetic is plain
+//   FP32 FMA plus one rsqrt per pair).  Per-tile partial sums are folded into
+//   the running sums with Kahan compensation.
+// The self pair i = j is evaluated like any other (it adds exactly 0 to the
+// acceleration) and its potential term -m_i/eps is removed at the end; with
+// eps = 0 a guarded variant skips r = 0 pairs.
+#pragma once
+
+#include "common.cuh"
+
+namespace treegb {
+
+constexpr int kWalkWarps = 4;                      // warps per block
+constexpr int kPPCap = 32 + 32 * kMaxLeafSmall;    // PP buffer entries per warp
+constexpr int kPCCap = 64;                         // PC buffer entries per warp
+
+struct WalkArgs {
+    int64_t n;
+    int32_t gs;
+    int64_t ngroups;
+    const void *spos;
+    const uint64_t *skey;
+    const uint32_t *perm;
+    const uint4 *ngeo;
+    const uint2 *nlink;
+    const void *mom_a, *mom_b, *mom_c;
+    const int64_t *dmac;
+    double G, eps, eps2;
+    void *a, *phi, *v;
+    double half_tau;
+    int32_t stack_depth;
+    uint4 *gstat;          // per group: {n_pc cells, n_pp particles, max stack, n_pp leaves}
+    int32_t *dstatus;
+    const int64_t *list_off;  // [2][ngroups+1] (emit mode)
+    int32_t *pc_list, *pp_list;
+};
+
+template <typename Real> __device__ __forceinline__ Real rsqrt_r(Real x);
+template <> __device__ __forceinline__ float rsqrt_r<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_r<double>(double x) { return rsqrt(x); }
+
+// Per-warp shared-memory slice, rounded up to 32 bytes so that every warp's
+// staging arrays (float4 / 32-byte double4) stay aligned.
+template <typename Real>
+__host__ __device__ constexpr size_t walk_warp_bytes(int stack_depth) {
+    return (((size_t)(stack_depth + kPPCap + kPCCap + 32) * 4 +
+             32 * (sizeof(typename Vec4<Real>::T) * 2 + sizeof(typename Vec2<Real>::T))) + 31) & ~(size_t)31;
+}
+
+// --- pair terms ------------------------------------------------------------
+// PP: source s = (x, y, z, m); d = r_s - r_i; accumulates m d / r^3 and -m / r.
+template <typename Real, bool SOFT>
+__device__ __forceinline__ void pp_term(Real px, Real py, Real pz, const typename Vec4<Real>::T &s,
+                                        Real eps2, Real (&acc)[4]) {
+    const Real dx = s.x - px, dy = s.y - py, dz = s.z - pz;
+    const Real r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+    Real rinv = rsqrt_r<Real>(r2);
+    if (!SOFT) rinv = r2 > Real(0) ? rinv : Real(0);
+    const Real mr = s.w * rinv;
+    const Real mr3 = mr * (rinv * rinv);
+    acc[0] = fma(mr3, dx, acc[0]);
+    acc[1] = fma(mr3, dy, acc[1]);
+    acc[2] = fma(mr3, dz, acc[2]);
+    acc[3] -= mr;
+}
+
+// PC: y = r_i - R, r_s^2 = |y|^2 + eps^2;
+//   a += -M y / r_s^3 + Q y / r_s^5 - 5/2 (y.Q.y) y / r_s^7
+//   phi += -M / r_s - 1/2 (y.Q.y) / r_s^5
+// A = (Rx, Ry, Rz, M), B = (Qxx, Qyy, Qzz, Qxy), C = (Qxz, Qyz).
+template <typename Real, bool QUAD, bool SOFT>
+__device__ __forceinline__ void pc_term(Real px, Real py, Real pz, const typename Vec4<Real>::T &A,
+                                        const typename Vec4<Real>::T &B, const typename Vec2<Real>::T &C,
+                                        Real eps2, Real (&acc)[4]) {
+    const Real yx = px - A.x, yy = py - A.y, yz = pz - A.z;
+    const Real r2 = fma(yx, yx, fma(yy, yy, fma(yz, yz, eps2)));
+    Real rinv = rsqrt_r<Real>(r2);
+    if (!SOFT) rinv = r2 > Real(0) ? rinv : Real(0);
+    const Real rinv2 = rinv * rinv;
+    const Real Mr = A.w * rinv;
+    const Real Mr3 = Mr * rinv2;
+    if (QUAD) {
+        const Real Qx = fma(B.x, yx, fma(B.w, yy, C.x * yz));
+        const Real Qy = fma(B.w, yx, fma(B.y, yy, C.y * yz));
+        const Real Qz = fma(C.x, yx, fma(C.y, yy, B.z * yz));
+        const Real yQy = fma(yx, Qx, fma(yy, Qy, yz * Qz));
+        const Real r3 = rinv * rinv2;
+        const Real r5 = r3 * rinv2;
+        const Real qr5 = yQy * r5;
+        const Real c = fma(Real(-2.5) * qr5, rinv2, -Mr3);
+        acc[0] = fma(c, yx, fma(r5, Qx, acc[0]));
+        acc[1] = fma(c, yy, fma(r5, Qy, acc[1]));
+        acc[2] = fma(c, yz, fma(r5, Qz, acc[2]));
+        acc[3] -= fma(Real(0.5), qr5, Mr);
+    } else {
+        acc[0] = fma(-Mr3, yx, acc[0]);
+        acc[1] = fma(-Mr3, yy, acc[1]);
+        acc[2] = fma(-Mr3, yz, acc[2]);
+        acc[3] -= Mr;
+    }
+}
+
+template <typename Real, bool KAHAN>
+__device__ __forceinline__ void fold(Real (&sum)[4], Real (&cmp)[4], const Real (&part)[4]) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (KAHAN) {
+            const Real y = part[c] - cmp[c];
+            const Real t = sum[c] + y;
+            cmp[c] = (t - sum[c]) - y;
+            sum[c] = t;
+        } else {
+            sum[c] += part[c];
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+template <typename Real, int TPL, bool QUAD, bool KAHAN, bool SOFT, int MODE>
+__global__ void __launch_bounds__(kWalkWarps * 32, 5) k_walk(const WalkArgs A) {
+    using V4 = typename Vec4<Real>::T;
+    using V2 = typename Vec2<Real>::T;
+    extern __shared__ __align__(32) unsigned char smem[];
+    __shared__ long long sD[kLevels];
+    if (threadIdx.x < kLevels) sD[threadIdx.x] = A.dmac[threadIdx.x];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int SD = A.stack_depth;
+    unsigned char *wb = smem + (size_t)warp * walk_warp_bytes<Real>(SD);
+    V4 *stA = reinterpret_cast<V4 *>(wb);
+    V4 *stB = stA + 32;
+    V2 *stC = reinterpret_cast<V2 *>(stB + 32);
+    uint32_t *stack = reinterpret_cast<uint32_t *>(stC + 32);
+    uint32_t *ppbuf = stack + SD;
+    uint32_t *pcbuf = ppbuf + kPPCap;
+    int *mark = reinterpret_cast<int *>(pcbuf + kPCCap);
+    const uint32_t lt = lanemask_lt();
+
+    const V4 *__restrict__ spos = reinterpret_cast<const V4 *>(A.spos);
+    const V4 *__restrict__ momA = reinterpret_cast<const V4 *>(A.mom_a);
+    const V4 *__restrict__ momB = reinterpret_cast<const V4 *>(A.mom_b);
+    const V2 *__restrict__ momC = reinterpret_cast<const V2 *>(A.mom_c);
+    const Real eps2 = (Real)A.eps2;
+
+    const int64_t g = (int64_t)blockIdx.x * kWalkWarps + warp;
+    if (g >= A.ngroups) return;
+    const int64_t s0 = g * A.gs;
+    const int64_t rem = A.n - s0;
+    const int cnt = rem < A.gs ? (int)rem : A.gs;
+
+    // targets and the group's integer box
+    Real px[TPL], py[TPL], pz[TPL], pm[TPL];
+    uint32_t lo0 = 0xffffffffu, lo1 = 0xffffffffu, lo2 = 0xffffffffu, hi0 = 0, hi1 = 0, hi2 = 0;
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+        const int li = lane + 32 * t;
+        px[t] = py[t] = pz[t] = pm[t] = Real(0);
+        if (li < cnt) {
+            const V4 p = spos[s0 + li];
+            px[t] = p.x; py[t] = p.y; pz[t] = p.z; pm[t] = p.w;
+            const uint64_t k = A.skey[s0 + li];
+            const uint32_t qx = compact3(k >> 2), qy = compact3(k >> 1), qz = compact3(k);
+            lo0 = min(lo0, qx); lo1 = min(lo1, qy); lo2 = min(lo2, qz);
+            hi0 = max(hi0, qx); hi1 = max(hi1, qy); hi2 = max(hi2, qz);
+        }
+    }
+    const int glo0 = (int)__reduce_min_sync(0xffffffffu, lo0), glo1 = (int)__reduce_min_sync(0xffffffffu, lo1),
+              glo2 = (int)__reduce_min_sync(0xffffffffu, lo2);
+    const int ghi0 = (int)__reduce_max_sync(0xffffffffu, hi0) + 1, ghi1 = (int)__reduce_max_sync(0xffffffffu, hi1) + 1,
+              ghi2 = (int)__reduce_max_sync(0xffffffffu, hi2) + 1;
+
+    Real sum[TPL][4], cmp[TPL][4];
+#pragma unroll
+    for (int t = 0; t < TPL; ++t)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { sum[t][c] = Real(0); cmp[t][c] = Real(0); }
+
+    // --- evaluation helpers (whole warp) ---
+    auto eval_pp_stage = [&](int ns) {
+        // sources already in stA[0..ns)
+        Real part[TPL][4];
+#pragma unroll
+        for (int t = 0; t < TPL; ++t)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) part[t][c] = Real(0);
+        if (ns == 32) {
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j) {
+                const V4 s = stA[j];
+#pragma unroll
+                for (int t = 0; t < TPL; ++t) pp_term<Real, SOFT>(px[t], py[t], pz[t], s, eps2, part[t]);
+            }
+        } else {
+            for (int j = 0; j < ns; ++j) {
+                const V4 s = stA[j];
+#pragma unroll
+                for (int t = 0; t < TPL; ++t) pp_term<Real, SOFT>(px[t], py[t], pz[t], s, eps2, part[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) fold<Real, KAHAN>(sum[t], cmp[t], part[t]);
+    };
+    auto eval_pp_list = [&](const uint32_t *buf, int ns) {
+        V4 s;
+        if (lane < ns) s = spos[buf[lane]];
+        __syncwarp();
+        if (lane < ns) stA[lane] = s;
+        __syncwarp();
+        eval_pp_stage(ns);
+        __syncwarp();
+    };
+    auto eval_pp_range = [&](uint32_t first, int ns) {
+        V4 s;
+        if (lane < ns) s = spos[first + lane];
+        __syncwarp();
+        if (lane < ns) stA[lane] = s;
+        __syncwarp();
+        eval_pp_stage(ns);
+        __syncwarp();
+    };
+    auto eval_pc_list = [&](const uint32_t *buf, int ns) {
+        if (lane < ns) {
+            const uint32_t c = buf[lane];
+            stA[lane] = momA[c];
+            if (QUAD) { stB[lane] = momB[c]; stC[lane] = momC[c]; }
+        }
+        __syncwarp();
+        Real part[TPL][4];
+#pragma unroll
+        for (int t = 0; t < TPL; ++t)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) part[t][c] = Real(0);
+        V4 b0{};
+        V2 c0{};
+        if (ns == 32) {
+#pragma unroll 4
+            for (int j = 0; j < 32; ++j) {
+                const V4 a = stA[j];
+                const V4 b = QUAD ? stB[j] : b0;
+                const V2 c = QUAD ? stC[j] : c0;
+#pragma unroll
+                for (int t = 0; t < TPL; ++t) pc_term<Real, QUAD, SOFT>(px[t], py[t], pz[t], a, b, c, eps2, part[t]);
+            }
+        } else {
+            for (int j = 0; j < ns; ++j) {
+                const V4 a = stA[j];
+                const V4 b = QUAD ? stB[j] : b0;
+                const V2 c = QUAD ? stC[j] : c0;
+#pragma unroll
+                for (int t = 0; t < TPL; ++t) pc_term<Real, QUAD, SOFT>(px[t], py[t], pz[t], a, b, c, eps2, part[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) fold<Real, KAHAN>(sum[t], cmp[t], part[t]);
+        __syncwarp();
+    };
+
+    // --- traversal ---
+    int64_t pc_base = 0, pp_base = 0;
+    if (MODE == kWalkEmit) {
+        pc_base = A.list_off[g];
+        pp_base = A.list_off[A.ngroups + 1 + g];
+    }
+    uint32_t n_pc = 0, n_pp = 0, n_ppl = 0, max_top = 1;
+    int top = 1, npc = 0, npp = 0;
+    // Stack entries are child ranges: first node | (count - 1) << 29.
+    if (lane == 0) stack[0] = 0u;  // the root: range (node 0, 1 node)
+    __syncwarp();
+    bool overflow = false;
+    while (top > 0) {
+        // pop up to 32 nodes from the top ranges; the last range may be split
+        const int nr = top < 32 ? top : 32;
+        uint32_t e = 0, sz = 0;
+        if (lane < nr) {
+            e = stack[top - 1 - lane];
+            sz = (e >> 29) + 1u;
+        }
+        const uint32_t incl0 = warp_incl_scan(sz, lane);
+        const uint32_t excl0 = incl0 - sz;
+        const uint32_t avail = __shfl_sync(0xffffffffu, incl0, 31);
+        const uint32_t take = avail < 32u ? avail : 32u;
+        const bool contrib = lane < nr && excl0 < take;
+        const int nfull = __popc(__ballot_sync(0xffffffffu, lane < nr && incl0 <= take));
+        mark[lane] = -1;
+        __syncwarp();
+        if (contrib) mark[excl0] = lane;
+        __syncwarp();
+        int owner = mark[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, owner, o);
+            if (lane >= o) owner = max(owner, y);
+        }
+        const uint32_t e_own = __shfl_sync(0xffffffffu, e, owner & 31);
+        const uint32_t x_own = __shfl_sync(0xffffffffu, excl0, owner & 31);
+        const bool act = (uint32_t)lane < take;
+        const uint32_t node = act ? (e_own & 0x1fffffffu) + ((uint32_t)lane - x_own) : 0u;
+        if (contrib && incl0 > take) {
+            // partially used range (lane == nfull): keep its unused tail on the stack
+            const uint32_t used = take - excl0;
+            stack[top - 1 - lane] = ((e & 0x1fffffffu) + used) | ((sz - used - 1u) << 29);
+        }
+        top -= nfull;
+        __syncwarp();
+        uint4 geo = make_uint4(0, 0, 0, 0);
+        uint2 lk = make_uint2(0, 0);
+        if (act) { geo = A.ngeo[node]; lk = A.nlink[node]; }
+        const int level = (int)(geo.w & 0xffu);
+        const bool leaf = (geo.w >> 8) & 1u;
+        const int s = 1 << (kBits - level);
+        const int cx = (int)geo.x, cy = (int)geo.y, cz = (int)geo.z;
+        const int gx = max(0, max(cx - ghi0, glo0 - (cx + s)));
+        const int gy = max(0, max(cy - ghi1, glo1 - (cy + s)));
+        const int gz = max(0, max(cz - ghi2, glo2 - (cz + s)));
+        const long long d2 = (long long)gx * gx + (long long)gy * gy + (long long)gz * gz;
+        const bool far = act && d2 >= sD[level];
+        const bool nleaf = act && !far && leaf;
+        const bool open = act && !far && !leaf;
+
+        // far cells
+        const uint32_t fm = __ballot_sync(0xffffffffu, far);
+        const uint32_t nf = __popc(fm);
+        if (MODE == kWalkForce) {
+            if (far) pcbuf[npc + __popc(fm & lt)] = node;
+            npc += nf;
+        } else if (MODE == kWalkEmit) {
+            if (far) A.pc_list[pc_base + n_pc + __popc(fm & lt)] = (int32_t)node;
+        }
+        n_pc += nf;
+
+        // children of opened cells: one stack entry per opened cell
+        const uint32_t om = __ballot_sync(0xffffffffu, open);
+        const int no = __popc(om);
+        if (top + no > SD) {
+            overflow = true;
+        } else {
+            if (open) stack[top + __popc(om & lt)] = lk.x | ((lk.y - 1u) << 29);
+            top += no;
+        }
+        max_top = max(max_top, (uint32_t)top);
+
+        // near leaves
+        const uint32_t lm = __ballot_sync(0xffffffffu, nleaf);
+        if (MODE == kWalkEmit) {
+            if (nleaf) A.pp_list[pp_base + n_ppl + __popc(lm & lt)] = (int32_t)node;
+        }
+        n_ppl += __popc(lm);
+        const uint32_t lc = nleaf ? lk.y : 0u;
+        const bool big = lc > (uint32_t)kMaxLeafSmall;
+        const uint32_t sc = big ? 0u : lc;
+        const uint32_t incl2 = warp_incl_scan(sc, lane);
+        const uint32_t tot2 = __shfl_sync(0xffffffffu, incl2, 31);
+        n_pp += __reduce_add_sync(0xffffffffu, lc);
+        if (MODE == kWalkForce) {
+            if (nleaf && !big)
+                for (uint32_t c = 0; c < lc; ++c) ppbuf[npp + (incl2 - lc) + c] = lk.x + c;
+            npp += (int)tot2;
+            __syncwarp();
+            uint32_t bm = __ballot_sync(0xffffffffu, big);
+            while (bm) {
+                const int b = __ffs(bm) - 1;
+                bm &= bm - 1;
+                const uint32_t f = __shfl_sync(0xffffffffu, lk.x, b);
+                const uint32_t c = __shfl_sync(0xffffffffu, lk.y, b);
+                for (uint32_t o = 0; o < c; o += 32) eval_pp_range(f + o, (int)min(32u, c - o));
+            }
+            if (npc >= 32) {
+                eval_pc_list(pcbuf, 32);
+                const int r = npc - 32;
+                uint32_t t = lane < r ? pcbuf[32 + lane] : 0;
+                __syncwarp();
+                if (lane < r) pcbuf[lane] = t;
+                __syncwarp();
+                npc = r;
+            }
+            if (npp >= 32) {
+                const int ntile = npp >> 5;
+                for (int t = 0; t < ntile; ++t) eval_pp_list(ppbuf + 32 * t, 32);
+                const int r = npp & 31;
+                uint32_t t = lane < r ? ppbuf[32 * ntile + lane] : 0;
+                __syncwarp();
+                if (lane < r) ppbuf[lane] = t;
+                __syncwarp();
+                npp = r;
+            }
+        } else {
+            __syncwarp();
+        }
+    }
+    if (MODE == kWalkForce) {
+        if (npc > 0) eval_pc_list(pcbuf, npc);
+        if (npp > 0) eval_pp_list(ppbuf, npp);
+    }
+    if (overflow && lane == 0) set_status(A.dstatus, TREE_DEV_STACK);
+    if (lane == 0 && A.gstat) A.gstat[g] = make_uint4(n_pc, n_pp, max_top, n_ppl);
+
+    if (MODE == kWalkForce) {
+        const Real G = (Real)A.G;
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) {
+            const int li = lane + 32 * t;
+            if (li < cnt) {
+                const uint32_t i = A.perm[s0 + li];
+                Real ax, ay, az, ph;
+                if (KAHAN) {
+                    ax = sum[t][0] - cmp[t][0]; ay = sum[t][1] - cmp[t][1];
+                    az = sum[t][2] - cmp[t][2]; ph = sum[t][3] - cmp[t][3];
+                } else {
+                    ax = sum[t][0]; ay = sum[t][1]; az = sum[t][2]; ph = sum[t][3];
+                }
+                if (SOFT) ph += pm[t] / (Real)A.eps;  // remove the self term -m_i / eps
+                ax *= G; ay *= G; az *= G; ph *= G;
+                Real *a = reinterpret_cast<Real *>(A.a);
+                const int64_t n = A.n;
+                a[i] = ax; a[n + i] = ay; a[2 * n + i] = az;
+                if (A.phi) reinterpret_cast<Real *>(A.phi)[i] = ph;
+                if (A.v) {
+                    Real *v = reinterpret_cast<Real *>(A.v);
+                    const Real ht = (Real)A.half_tau;
+                    v[i] = fma(ht, ax, v[i]);
+                    v[n + i] = fma(ht, ay, v[n + i]);
+                    v[2 * n + i] = fma(ht, az, v[2 * n + i]);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace treegb
+
+namespace treegb {
+
+// Host: walk arguments from the workspace.
+inline WalkArgs make_walk_args(TreeWorkspace *ws, const WalkOut &out) {
+    WalkArgs a;
+    a.n = ws->n;
+    a.gs = ws->p.group_size;
+    a.ngroups = (ws->n + ws->p.group_size - 1) / ws->p.group_size;
+    a.spos = ws->spos;
+    a.skey = ws->key;
+    a.perm = ws->idx;
+    a.ngeo = ws->ngeo;
+    a.nlink = ws->nlink;
+    a.mom_a = ws->mom_a;
+    a.mom_b = ws->mom_b;
+    a.mom_c = ws->mom_c;
+    a.dmac = ws->dmac;
+    a.G = ws->p.G;
+    a.eps = ws->p.eps;
+    a.eps2 = ws->p.eps * ws->p.eps;
+    a.a = out.a;
+    a.phi = out.phi;
+    a.v = out.v;
+    a.half_tau = out.half_tau;
+    a.stack_depth = ws->p.stack_depth;
+    a.gstat = ws->gstat;
+    a.dstatus = ws->dstatus;
+    a.list_off = ws->list_cnt;
+    a.pc_list = ws->pc_list;
+    a.pp_list = ws->pp_list;
+    return a;
+}
+
+template <typename Real, int TPL, bool QUAD, bool KAHAN, bool SOFT, int MODE>
+cudaError_t walk_run(TreeWorkspace *ws, const WalkArgs &a, cudaStream_t s) {
+    if (a.ngroups <= 0) return cudaSuccess;
+    auto k = k_walk<Real, TPL, QUAD, KAHAN, SOFT, MODE>;
+    const size_t smem = kWalkWarps * walk_warp_bytes<Real>(a.stack_depth);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned nb = (unsigned)((a.ngroups + kWalkWarps - 1) / kWalkWarps);
+    k<<<nb, kWalkWarps * 32, smem, s>>>(a);
+    ws->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace treegb
