@@ -207,6 +207,25 @@ tree_status_t tree_timing_enable(TreeWorkspace *ws, int32_t enable);
  * number of kernels launched inside the timed phases. */
 tree_status_t tree_timing_read(TreeWorkspace *ws, double *ms, int64_t *calls, int64_t *launches);
 
+/* Direct summation like tree_direct_forces, for callers that cannot allocate
+ * device memory: it needs no workspace and calls no allocator.  This entry
+ * has no counterpart in the paper; it exists for applications whose own
+ * memory pool owns the GPU, or code that may only touch buffers it is given.
+ * x [3][n], m [n] of dtype; targets device int64[nt]; G, eps as in Eq. 1;
+ * a_out device double [3][nt]; phi_out device double [nt] or NULL.
+ * Scratch is a fixed 4 MiB array inside the library, present on every GPU
+ * that loads it until the process exits.  At most TREE_NOALLOC_MAX_TARGETS
+ * targets per call (TREE_ERR_CAPACITY beyond); any n >= 1 sources.
+ * The first call on each device looks up that array's device address (make
+ * it before any stream capture).  All calls share the one array: calls that
+ * may overlap on the GPU (different streams, or different host threads)
+ * race and give wrong results; serialise them.  Nothing needs clearing
+ * between calls: every scratch entry is written before it is read. */
+#define TREE_NOALLOC_MAX_TARGETS 4096
+tree_status_t tree_direct_forces_noalloc(const void *x, const void *m, int64_t n, int32_t dtype, double G,
+                                         double eps, const int64_t *targets, int64_t nt, double *a_out,
+                                         double *phi_out, void *stream);
+
 /* Synchronises the device, returns TREE_OK if the device status word is 0,
  * else TREE_ERR_DEVICE; *status (host) receives the word.  clear != 0 resets
  * it to 0 afterwards. */

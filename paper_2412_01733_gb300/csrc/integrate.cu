@@ -4,6 +4,8 @@
 #include <float.h>
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace treegb {
@@ -230,6 +232,41 @@ cudaError_t launch_direct(TreeWorkspace *ws, const void *x, const void *m, int64
     return cudaGetLastError();
 }
 
+// ============================================================== direct sum without allocation
+// tree_direct_forces needs a workspace, and the workspace allocates its
+// scratch with cudaMalloc.  Callers that must not allocate device memory
+// (for example an application whose memory pool owns the whole GPU, or code
+// that may only use buffers it was handed) call tree_direct_forces_noalloc
+// instead: the per-chunk partial sums live in this fixed module array, which
+// every GPU that loads the library holds (4 MiB) until the process exits.
+constexpr int64_t kNoAllocScratchDoubles = 524288;  // 4 MiB
+static_assert(kNoAllocScratchDoubles >= 4 * (int64_t)TREE_NOALLOC_MAX_TARGETS, "scratch too small");
+__device__ __align__(256) double g_noalloc_part[kNoAllocScratchDoubles];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_part on the current device (looked up once per
+// device; host code cannot use the array's name as a device pointer).
+cudaError_t noalloc_scratch(double **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_part);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
 // ============================================================== per-group walk records
 // gstat[g] = {n_pc cells, n_pp particles, max stack, n_pp leaves}.
 // Pair totals: sum_g |g| n_pc and sum_g |g| n_pp; deepest stack.
@@ -318,3 +355,42 @@ cudaError_t launch_gstat_reduce(TreeWorkspace *ws, int64_t ngroups, cudaStream_t
 }
 
 }  // namespace treegb
+
+extern "C" tree_status_t tree_direct_forces_noalloc(const void *x, const void *m, int64_t n, int32_t dtype,
+                                                    double G, double eps, const int64_t *targets, int64_t nt,
+                                                    double *a_out, double *phi_out, void *stream) {
+    using namespace treegb;
+    if (n < 0 || nt < 0) return TREE_ERR_ARG;
+    if (dtype != TREE_F32 && dtype != TREE_F64) return TREE_ERR_ARG;
+    if (!(eps >= 0.0) || !isfinite(eps) || !isfinite(G)) return TREE_ERR_ARG;
+    if (nt > TREE_NOALLOC_MAX_TARGETS) return TREE_ERR_CAPACITY;
+    if (nt == 0) return TREE_OK;
+    if (!x || !m || !targets || !a_out || n < 1) return TREE_ERR_ARG;
+    double *part = nullptr;
+    if (noalloc_scratch(&part) != cudaSuccess) return TREE_ERR_CUDA;
+    // same chunking as tree_direct_forces, capped so the partials fit the array
+    const int64_t tt = (nt + kDirThreads - 1) / kDirThreads;
+    int64_t nch = (152 * 16 + tt - 1) / tt;
+    const int64_t maxch = (n + kDirThreads - 1) / kDirThreads;
+    const int64_t fit = kNoAllocScratchDoubles / (4 * nt);
+    if (nch > maxch) nch = maxch;
+    if (nch > fit) nch = fit;
+    if (nch < 1) nch = 1;
+    int64_t chunk = (n + nch - 1) / nch;
+    chunk = ((chunk + kDirThreads - 1) / kDirThreads) * kDirThreads;
+    nch = (n + chunk - 1) / chunk;
+    if (nch < 1) nch = 1;
+    // every partial slot [chunk][component][target] is written exactly once
+    // before it is read, so the array needs no clearing between calls
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    dim3 grid((unsigned)tt, (unsigned)nch);
+    const double eps2 = eps * eps;
+    if (dtype == TREE_F64)
+        k_direct<double><<<grid, kDirThreads, 0, s>>>((const double *)x, (const double *)m, n, targets, nt, chunk,
+                                                      eps2, part);
+    else
+        k_direct<float><<<grid, kDirThreads, 0, s>>>((const float *)x, (const float *)m, n, targets, nt, chunk, eps2,
+                                                     part);
+    k_direct_final<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(part, nt, (int)nch, G, a_out, phi_out);
+    return cudaGetLastError() == cudaSuccess ? TREE_OK : TREE_ERR_CUDA;
+}

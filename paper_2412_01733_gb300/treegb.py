@@ -66,6 +66,7 @@ _SIGNATURES = {
     "tree_export_moments": [_vp, _vp, _vp, _vp, _vp],
     "tree_export_lists": [_vp, _vp, _vp, _vp, _vp, _vp],
     "tree_mac_table": [_dbl, ctypes.POINTER(_i64)],
+    "tree_direct_forces_noalloc": [_vp, _vp, _i64, _i32, _dbl, _dbl, _vp, _i64, _vp, _vp, _vp],
     "tree_timing_enable": [_vp, _i32],
     "tree_timing_read": [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
     "tree_status_string": [_i32],
