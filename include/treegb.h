@@ -22,7 +22,9 @@
  *   octree node 0 = root; a node is internal iff count > leaf_cap and level < 21;
  *          children are the non-empty octants in octant order; breadth-first
  *          numbering (level by level, ascending key prefix within a level).
- *   groups group g = sorted particles [g*Gs, min((g+1)*Gs, N)), integer box
+ *   groups chunks of Gs consecutive sorted particles, cut between neighbours
+ *          i-1, i whose keys share fewer octal digits than
+ *          max(leaf level(i-1), leaf level(i)) - group_split; integer box
  *          [min q, max q + 1) per axis.
  *   MAC    a node of level l (side s = 2^(21-l), box [c, c+s)) is far for a group
  *          iff s^2 < fl(theta^2 * d2), d2 = sum_d max(0, c_d - ghi_d, glo_d - c_d - s)^2
@@ -93,6 +95,8 @@ typedef struct {
     int32_t stack_depth; /* walk stack entries per warp, 256..8192, a multiple of 32 */
     int32_t precision;   /* TREE_F32 or TREE_F64 */
     int32_t kahan;       /* FP32: 1 = compensated per-particle accumulation */
+    int32_t group_split; /* delta: cut a group between neighbours that do not share the cell
+                            delta levels above the finer of their leaves; 0 = plain chunks */
     int64_t node_cap;    /* node array capacity; 0 = default from n_max and leaf_cap */
 } TreeParams;
 
@@ -130,7 +134,7 @@ typedef struct {
 
 /* Fills *p with the defaults: G = 1, eps = 0.01, theta = 0.7, order = 2,
  * leaf_cap = 16, group_size = 32, stack_depth = 1024, precision = TREE_F32,
- * kahan = 1, node_cap = 0. */
+ * kahan = 1, group_split = 3, node_cap = 0. */
 tree_status_t tree_params_default(TreeParams *p);
 
 /* Allocates a workspace for up to n_max particles on the current device.
@@ -254,6 +258,17 @@ tree_status_t tree_export_moments(TreeWorkspace *ws, double *M, double *R, doubl
  * group, entries are in walk order, not sorted. */
 tree_status_t tree_export_lists(TreeWorkspace *ws, int64_t *pc_off, int32_t *pc_list,
                                 int64_t *pp_off, int32_t *pp_list, void *stream);
+
+/* Copies the per-group records of the last walk into a caller device buffer
+ * out (uint32 [4][n_groups]): row 0 far cells (PC list length), row 1 near
+ * particles (PP sources, self included), row 2 deepest walk stack, row 3
+ * near leaves. */
+tree_status_t tree_export_group_stats(TreeWorkspace *ws, uint32_t *out, void *stream);
+
+/* Copies the walk groups of the last tree_build into gfirst (device
+ * uint32[n_groups + 1]): group g is sorted particles [gfirst[g], gfirst[g+1]),
+ * gfirst[n_groups] = n.  Synchronises to read n_groups. */
+tree_status_t tree_export_groups(TreeWorkspace *ws, uint32_t *gfirst, void *stream);
 
 /* Host only, no device work: the integer thresholds D_l (l = 0..21) with
  * "node of level l is far" <=> d2 >= D_l, where D_l = min{d : s_l^2 < fl(theta^2 d)}.

@@ -18,6 +18,7 @@
  *   orc_moments       mass, centre of mass and traceless quadrupole per cell
  *                     (Sec. 2: far groups act through their total mass at the
  *                     centre of mass; the quadrupole is the next term).
+ *   orc_groups        walk groups: key-order chunks, cut at coarse jumps.
  *   orc_lists         group walk with the theta opening criterion (Sec. 2).
  *   orc_tree_forces   cell expansion for accepted cells + exact PP sum for the
  *                     near leaves, self term excluded (Eq. 1).
@@ -268,9 +269,44 @@ void orc_moments(int64_t nn, const int64_t *first, const int64_t *count,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Walk groups.  Particles are taken in key order in chunks of gs; a chunk is
+ * further cut between consecutive particles i, i+1 that do not share the cell
+ * delta levels above the finer of their two leaves, i.e. where
+ *   P(i, i+1) < max(leaf_level(i), leaf_level(i+1)) - delta,
+ * P = number of leading octal digits the two keys share (21 if equal).
+ * delta = 0 keeps plain chunks.  gfirst (capacity n + 1) receives the first
+ * sorted index of every group and n at the end; returns the group count. */
+int64_t orc_groups(int64_t n, const uint64_t *skey, int64_t nn, const int32_t *level, const int64_t *first,
+                   const int64_t *count, const int32_t *nchild, int32_t gs, int32_t delta, int64_t *gfirst)
+{
+    int32_t *lv = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t c = 0; c < nn; ++c)
+        if (nchild[c] == 0)
+            for (int64_t s = first[c]; s < first[c] + count[c]; ++s) lv[s] = level[c];
+    int64_t ng = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int start = (i % gs) == 0;
+        if (!start && delta > 0) {
+            uint64_t d = skey[i - 1] ^ skey[i];
+            int common = 21;
+            if (d) {
+                int hb = 63 - __builtin_clzll(d);
+                common = (62 - hb) / 3;
+            }
+            int lmax = lv[i - 1] > lv[i] ? lv[i - 1] : lv[i];
+            if (common < lmax - delta) start = 1;
+        }
+        if (start) gfirst[ng++] = i;
+    }
+    gfirst[ng] = n;
+    free(lv);
+    return ng;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Group walk with the opening criterion.
- *   Group g = sorted particles [g gs, min((g+1) gs, n)); its integer box is
- *   [min q_d, max q_d + 1) per axis.  Node C at level l has side s = 2^(21-l)
+ *   Group g = sorted particles [gfirst[g], gfirst[g+1]) (orc_groups); its
+ *   integer box is [min q_d, max q_d + 1) per axis.  Node C at level l has side s = 2^(21-l)
  *   and box [c_d, c_d + s).  gap_d = max(0, c_d - ghi_d, glo_d - (c_d + s)),
  *   d2 = sum gap_d^2.  C is accepted as far iff s^2 < theta^2 d2 (FP64, with
  *   theta^2 = theta * theta rounded once); equality opens.  From the root:
@@ -280,18 +316,17 @@ void orc_moments(int64_t nn, const int64_t *first, const int64_t *count,
  * qs: (3, n) quantised coordinates in SORTED order.
  * Call once with pc_list = pp_list = NULL to get the offsets (CSR, ngroups+1
  * entries each), then again with lists of the sizes pc_off[ng], pp_off[ng]. */
-void orc_lists(int64_t n, const uint32_t *qs, int32_t gs, double theta,
+void orc_lists(int64_t n, const uint32_t *qs, int64_t ng, const int64_t *gfirst, double theta,
                int64_t nn, const int32_t *level, const uint32_t *corner /* (3, nn) */,
                const int64_t *child, const int32_t *nchild,
                int64_t *pc_off, int64_t *pp_off, int64_t *pc_list, int64_t *pp_list)
 {
-    const int64_t ng = (n + gs - 1) / gs;
     const double th2 = theta * theta;
     int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nn > 0 ? nn : 1));
     int64_t npc = 0, npp = 0;
     for (int64_t g = 0; g < ng; ++g) {
         pc_off[g] = npc; pp_off[g] = npp;
-        int64_t s0 = g * gs, s1 = (g + 1) * gs < n ? (g + 1) * gs : n;
+        int64_t s0 = gfirst[g], s1 = gfirst[g + 1];
         int64_t glo[3], ghi[3];
         for (int d = 0; d < 3; ++d) {
             uint32_t mn = qs[d * n + s0], mx = qs[d * n + s0];
@@ -339,17 +374,16 @@ void orc_lists(int64_t n, const uint32_t *qs, int32_t gs, double theta,
  * (monopole: Q = 0).  PP part: Eq. 1 over the members of each near leaf,
  * j != i.  x, m in original order; outputs in original order. */
 void orc_tree_forces(int64_t n, const double *x, const double *m, const int64_t *perm,
-                     int32_t gs, int64_t nn, const double *M, const double *R, const double *Q,
+                     int64_t ng, const int64_t *gfirst, int64_t nn, const double *M, const double *R, const double *Q,
                      const int64_t *first, const int64_t *count,
                      const int64_t *pc_off, const int64_t *pc_list,
                      const int64_t *pp_off, const int64_t *pp_list,
                      double G, double eps, int32_t quad, double *a, double *phi)
 {
     const double eps2 = eps * eps;
-    const int64_t ng = (n + gs - 1) / gs;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t g = 0; g < ng; ++g) {
-        int64_t s0 = g * gs, s1 = (g + 1) * gs < n ? (g + 1) * gs : n;
+        int64_t s0 = gfirst[g], s1 = gfirst[g + 1];
         for (int64_t s = s0; s < s1; ++s) {
             int64_t i = perm[s];
             double xi = x[i], yi = x[n + i], zi = x[2 * n + i];

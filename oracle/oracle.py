@@ -43,9 +43,11 @@ def lib():
         L.orc_octree.argtypes = [i64, _U64, i32, i64, _I32, _U32, _I64, _I64, _I64, _I32]
         L.orc_octree.restype = i64
         L.orc_moments.argtypes = [i64, _I64, _I64, _D, _I64, i64, _D, _D, _D, _D, _D]
-        L.orc_lists.argtypes = [i64, _U32, i32, dbl, i64, _I32, _U32, _I64, _I32,
+        L.orc_groups.argtypes = [i64, _U64, i64, _I32, _I64, _I64, _I32, i32, i32, _I64]
+        L.orc_groups.restype = i64
+        L.orc_lists.argtypes = [i64, _U32, i64, _I64, dbl, i64, _I32, _U32, _I64, _I32,
                                 _I64, _I64, _I64, _I64]
-        L.orc_tree_forces.argtypes = [i64, _D, _D, _I64, i32, i64, _D, _D, _D, _I64, _I64,
+        L.orc_tree_forces.argtypes = [i64, _D, _D, _I64, i64, _I64, i64, _D, _D, _D, _I64, _I64,
                                       _I64, _I64, _I64, _I64, dbl, dbl, i32, _D, _D]
         L.orc_threads.restype = ctypes.c_int
         L.orc_set_threads.argtypes = [ctypes.c_int]
@@ -164,13 +166,24 @@ def moments(tree: Octree, perm, x, m, lo, k):
     return M, R, Q
 
 
-def lists(qs, gs, theta, tree: Octree):
+def groups(skey, tree: Octree, gs, delta=3):
+    """First sorted index of every walk group, plus n at the end (orc_groups)."""
+    skey = np.ascontiguousarray(skey, dtype=np.uint64)
+    n = skey.shape[0]
+    gf = np.zeros(n + 1, np.int64)
+    ng = lib().orc_groups(n, _p(skey, _U64), tree.nn, _p(tree.level, _I32), _p(tree.first, _I64),
+                          _p(tree.count, _I64), _p(tree.nchild, _I32), int(gs), int(delta), _p(gf, _I64))
+    return gf[: ng + 1].copy()
+
+
+def lists(qs, gfirst, theta, tree: Octree):
     """CSR interaction lists per group: (pc_off, pc_list, pp_off, pp_list)."""
     qs = np.ascontiguousarray(qs, dtype=np.uint32)
+    gfirst = np.ascontiguousarray(gfirst, dtype=np.int64)
     n = qs.shape[1]
-    ng = (n + gs - 1) // gs
+    ng = gfirst.shape[0] - 1
     pc_off = np.zeros(ng + 1, np.int64); pp_off = np.zeros(ng + 1, np.int64)
-    args = (n, _p(qs, _U32), int(gs), float(theta), tree.nn, _p(tree.level, _I32),
+    args = (n, _p(qs, _U32), ng, _p(gfirst, _I64), float(theta), tree.nn, _p(tree.level, _I32),
             _p(tree.corner, _U32), _p(tree.child, _I64), _p(tree.nchild, _I32))
     lib().orc_lists(*args, _p(pc_off, _I64), _p(pp_off, _I64), None, None)
     pc = np.zeros(max(1, pc_off[-1]), np.int64); pp = np.zeros(max(1, pp_off[-1]), np.int64)
@@ -189,6 +202,7 @@ class TreeResult:
     M: np.ndarray
     R: np.ndarray
     Q: np.ndarray
+    gfirst: np.ndarray    # walk groups: first sorted index of each, then n
     pc_off: np.ndarray
     pc_list: np.ndarray
     pp_off: np.ndarray
@@ -197,7 +211,7 @@ class TreeResult:
     phi: np.ndarray       # (n,)
 
 
-def tree_forces(x, m, *, G=1.0, eps=0.0, theta=0.7, lcap=16, gs=32, quad=True,
+def tree_forces(x, m, *, G=1.0, eps=0.0, theta=0.7, lcap=16, gs=32, quad=True, delta=3,
                 want_forces=True):
     """Whole canonical tree pipeline; returns every intermediate and a, phi."""
     x = _f64(x); m = _f64(m)
@@ -208,15 +222,16 @@ def tree_forces(x, m, *, G=1.0, eps=0.0, theta=0.7, lcap=16, gs=32, quad=True,
     tr = octree(key[perm], lcap)
     M, R, Q = moments(tr, perm, x, m, lo, k)
     qs = np.ascontiguousarray(q[:, perm])
-    pc_off, pc, pp_off, pp = lists(qs, gs, theta, tr)
+    gf = groups(key[perm], tr, gs, delta)
+    pc_off, pc, pp_off, pp = lists(qs, gf, theta, tr)
     a = np.zeros((3, n)); phi = np.zeros(n)
     if want_forces:
-        lib().orc_tree_forces(n, _p(x, _D), _p(m, _D), _p(perm, _I64), int(gs), tr.nn,
+        lib().orc_tree_forces(n, _p(x, _D), _p(m, _D), _p(perm, _I64), gf.shape[0] - 1, _p(gf, _I64), tr.nn,
                               _p(M, _D), _p(R, _D), _p(Q, _D), _p(tr.first, _I64),
                               _p(tr.count, _I64), _p(pc_off, _I64), _p(pc, _I64),
                               _p(pp_off, _I64), _p(pp, _I64), float(G), float(eps),
                               1 if quad else 0, _p(a, _D), _p(phi, _D))
-    return TreeResult(lo, k, q, key, perm, tr, M, R, Q, pc_off, pc, pp_off, pp, a, phi)
+    return TreeResult(lo, k, q, key, perm, tr, M, R, Q, gf, pc_off, pc, pp_off, pp, a, phi)
 
 
 def tree_accel(x, m, **kw):

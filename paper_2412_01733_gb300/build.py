@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtreegb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "build.cu", "moments.cu", "integrate.cu", "walk_f32.cu", "walk_f64.cu"]
+SOURCES = ["api.cu", "build.cu", "groups.cu", "moments.cu", "integrate.cu", "walk_f32.cu", "walk_f64.cu"]
 
 
 def nvcc() -> str:
@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
             if verbose and err:
                 print(err)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+    cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-Xlinker", "--no-undefined", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stderr)

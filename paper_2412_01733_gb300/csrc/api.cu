@@ -31,6 +31,7 @@ tree_status_t check_params(const TreeParams *p) {
     if (p->stack_depth < 256 || p->stack_depth > 8192 || p->stack_depth % 32) return TREE_ERR_ARG;
     if (p->precision != TREE_F32 && p->precision != TREE_F64) return TREE_ERR_ARG;
     if (p->kahan != 0 && p->kahan != 1) return TREE_ERR_ARG;
+    if (p->group_split < 0 || p->group_split > kMaxLevel) return TREE_ERR_ARG;
     if (p->node_cap < 0 || p->node_cap >= kMaxNodes) return TREE_ERR_ARG;
     return TREE_OK;
 }
@@ -69,7 +70,8 @@ void free_all(TreeWorkspace *ws) {
     void *ptrs[] = {ws->key, ws->key_alt, ws->idx, ws->idx_alt, ws->hist, ws->sort_status, ws->level_status,
                     ws->ctr, ws->part, ws->box, ws->spos, ws->nfirst, ws->ncount, ws->ngeo, ws->nlink,
                     ws->mom64, ws->mom_a, ws->mom_b, ws->mom_c, ws->dstatus, ws->stats, ws->gstat,
-                    ws->list_cnt, ws->pc_list, ws->pp_list, ws->direct_part, ws->dmac};
+                    ws->list_cnt, ws->pc_list, ws->pp_list, ws->direct_part, ws->dmac, ws->gorder,
+                    ws->gkey, ws->gbucket, ws->gfirst, ws->plev, ws->ccount, ws->coff, ws->gscan_status};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : ws->ev) cudaEventDestroy(e);
@@ -152,6 +154,7 @@ tree_status_t tree_params_default(TreeParams *p) {
     p->stack_depth = 1024;
     p->precision = TREE_F32;
     p->kahan = 1;
+    p->group_split = 3;
     p->node_cap = 0;
     return TREE_OK;
 }
@@ -179,7 +182,8 @@ tree_status_t tree_workspace_create(int64_t n_max, const TreeParams *p, TreeWork
     const size_t NC = (size_t)ws->node_cap;
     ws->sort_tiles_max = (n_max + kSortTile - 1) / kSortTile + 1;
     ws->level_tiles_max = (ws->node_cap + kLevelThreads - 1) / kLevelThreads + 1;
-    ws->groups_max = (n_max + 15) / 16 + 1;
+    ws->groups_max = n_max + 1;  // a group holds at least one particle
+    const int64_t chunks_max = (n_max + 15) / 16 + 1;
     const size_t v4 = p->precision == TREE_F64 ? sizeof(double4a) : sizeof(float4);
     const size_t v2 = p->precision == TREE_F64 ? sizeof(double2a) : sizeof(float2);
     bool ok = dalloc(&ws->key, N) && dalloc(&ws->key_alt, N) && dalloc(&ws->idx, N) && dalloc(&ws->idx_alt, N) &&
@@ -192,6 +196,10 @@ tree_status_t tree_workspace_create(int64_t n_max, const TreeParams *p, TreeWork
               dalloc((unsigned char **)&ws->mom_a, NC * v4) && dalloc((unsigned char **)&ws->mom_b, NC * v4) &&
               dalloc((unsigned char **)&ws->mom_c, NC * v2) && dalloc(&ws->dstatus, 1) &&
               dalloc(&ws->stats, kStatCount) && dalloc(&ws->gstat, (size_t)ws->groups_max) &&
+              dalloc(&ws->gorder, (size_t)ws->groups_max) && dalloc(&ws->gkey, (size_t)ws->groups_max) &&
+              dalloc(&ws->gbucket, 64) && dalloc(&ws->gfirst, (size_t)ws->groups_max + 1) &&
+              dalloc(&ws->plev, N) && dalloc(&ws->ccount, (size_t)chunks_max) && dalloc(&ws->coff, (size_t)chunks_max) &&
+              dalloc(&ws->gscan_status, (size_t)(chunks_max / 2048 + 2)) &&
               dalloc(&ws->dmac, kLevels);
     if (!ok) {
         free_all(ws);
@@ -222,11 +230,16 @@ tree_status_t tree_set_params(TreeWorkspace *ws, const TreeParams *p) {
     tree_status_t st = check_params(p);
     if (st != TREE_OK) return st;
     if (p->leaf_cap != ws->p.leaf_cap || p->precision != ws->p.precision) return TREE_ERR_ARG;
-    const bool regroup = p->group_size != ws->p.group_size;
+    const bool regroup = p->group_size != ws->p.group_size || p->group_split != ws->p.group_split;
     const int64_t keep_cap = ws->p.node_cap;
     ws->p = *p;
     ws->p.node_cap = keep_cap;
-    if (regroup) ws->list_groups = -1;
+    if (regroup) {
+        // the walk groups come from the tree build: a new grouping needs a new build
+        ws->list_groups = -1;
+        ws->built = false;
+        ws->has_moments = false;
+    }
     return TREE_OK;
 }
 
@@ -270,6 +283,7 @@ tree_status_t tree_build(TreeWorkspace *ws, const void *x, int64_t n, int32_t dt
     {
         PhaseScope ph(ws, TREE_PHASE_OCTREE, s);
         TRY_CUDA(launch_octree(ws, n, s));
+        TRY_CUDA(launch_groups(ws, n, s));
     }
     ws->built = true;
     return TREE_OK;
@@ -297,13 +311,18 @@ static tree_status_t walk(TreeWorkspace *ws, int mode, const WalkOut &out, cudaS
     tree_status_t st = upload_mac(ws, s);
     if (st != TREE_OK) return st;
     PhaseScope ph(ws, mode == kWalkForce ? TREE_PHASE_WALK : TREE_PHASE_LISTS, s);
+    TRY_CUDA(launch_group_order(ws, s));
     if (ws->p.precision == TREE_F64) TRY_CUDA(launch_walk_f64(ws, mode, out, s));
     else TRY_CUDA(launch_walk_f32(ws, mode, out, s));
     return TREE_OK;
 }
 
 static tree_status_t build_lists(TreeWorkspace *ws, cudaStream_t s) {
-    const int64_t ng = (ws->n + ws->p.group_size - 1) / ws->p.group_size;
+    uint32_t ngd = 0;
+    TRY_CUDA(cudaMemcpyAsync(&ngd, ws->ctr + kCtrGroups, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    const int64_t ng = ngd;
+    ws->list_groups_host = ng;
     WalkOut none{nullptr, nullptr, nullptr, 0.0};
     tree_status_t st = walk(ws, kWalkCount, none, s);
     if (st != TREE_OK) return st;
@@ -399,6 +418,7 @@ tree_status_t leapfrog_step(TreeWorkspace *ws, void *x, void *v, const void *m, 
     {
         PhaseScope ph(ws, TREE_PHASE_OCTREE, s);
         TRY_CUDA(launch_octree(ws, n, s));
+        TRY_CUDA(launch_groups(ws, n, s));
     }
     ws->built = true;
     {
@@ -476,7 +496,7 @@ tree_status_t tree_get_info(TreeWorkspace *ws, TreeInfo *info) {
     memset(info, 0, sizeof(*info));
     TRY_CUDA(cudaDeviceSynchronize());
     info->n = ws->n;
-    info->n_groups = ws->n > 0 ? (ws->n + ws->p.group_size - 1) / ws->p.group_size : 0;
+    info->n_groups = 0;
     info->list_pc = ws->list_groups >= 0 ? ws->list_pc : 0;
     info->list_pp = ws->list_groups >= 0 ? ws->list_pp : 0;
     info->launches = ws->launches;
@@ -490,6 +510,7 @@ tree_status_t tree_get_info(TreeWorkspace *ws, TreeInfo *info) {
     info->depth = 0;
     for (int l = 0; l < kLevels; ++l)
         if (info->level_offset[l + 1] > info->level_offset[l]) info->depth = l;
+    info->n_groups = ctr[kCtrGroups];
     info->box_k = box.k;
     for (int d = 0; d < 3; ++d) info->box_lo[d] = box.lo[d];
     if (ws->has_moments) {
@@ -532,6 +553,28 @@ tree_status_t tree_export_moments(TreeWorkspace *ws, double *M, double *R, doubl
         if (R) TRY_CUDA(cudaMemcpyAsync(R + d * nn, ws->mom64 + (1 + d) * cap, nn * 8, cudaMemcpyDeviceToDevice, s));
     for (int c = 0; c < 6; ++c)
         if (Q) TRY_CUDA(cudaMemcpyAsync(Q + c * nn, ws->mom64 + (4 + c) * cap, nn * 8, cudaMemcpyDeviceToDevice, s));
+    return TREE_OK;
+}
+
+tree_status_t tree_export_group_stats(TreeWorkspace *ws, uint32_t *out, void *stream) {
+    if (!ws || !out) return TREE_ERR_ARG;
+    if (!ws->has_moments) return TREE_ERR_STATE;
+    uint32_t ng = 0;
+    TRY_CUDA(cudaDeviceSynchronize());
+    TRY_CUDA(cudaMemcpy(&ng, ws->ctr + kCtrGroups, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    TRY_CUDA(launch_export_gstat(ws, ng, out, as_stream(stream)));
+    return TREE_OK;
+}
+
+tree_status_t tree_export_groups(TreeWorkspace *ws, uint32_t *gfirst, void *stream) {
+    if (!ws || !gfirst) return TREE_ERR_ARG;
+    if (!ws->built) return TREE_ERR_STATE;
+    if (ws->n == 0) return TREE_OK;
+    uint32_t ng = 0;
+    TRY_CUDA(cudaDeviceSynchronize());
+    TRY_CUDA(cudaMemcpy(&ng, ws->ctr + kCtrGroups, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    TRY_CUDA(cudaMemcpyAsync(gfirst, ws->gfirst, ((size_t)ng + 1) * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                             as_stream(stream)));
     return TREE_OK;
 }
 

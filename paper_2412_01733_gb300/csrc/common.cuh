@@ -60,7 +60,10 @@ enum CounterSlots {
     kCtrLevelStart = kCtrLevelTicket + 24,    // 23 level starts
     kCtrLevelRawEnd = kCtrLevelStart + 24,    // 23 raw ends
     kCtrLevelTrunc = kCtrLevelRawEnd + 24,    // 23 truncation points
-    kCtrCount = kCtrLevelTrunc + 24
+    kCtrGroups = kCtrLevelTrunc + 24,         // number of walk groups
+    kCtrGScanTicket = kCtrGroups + 1,         // group-count scan tiles
+    kCtrWalkTicket = kCtrGroups + 2,          // walk: next group slot (reset before every walk)
+    kCtrCount = kCtrGroups + 8
 };
 
 // Statistics slots (unsigned long long), cleared at the start of each walk.
@@ -103,12 +106,22 @@ struct TreeWorkspace {
     int32_t *dstatus = nullptr;
     unsigned long long *stats = nullptr;
     uint4 *gstat = nullptr;            // per walk group: {n_pc, n_pp particles, max stack, n_pp leaves}
+    uint32_t *gfirst = nullptr;        // walk groups: first sorted index of each, then n
+    uint8_t *plev = nullptr;           // leaf level of every sorted particle
+    uint32_t *ccount = nullptr, *coff = nullptr;  // groups starting in each Gs chunk / their offsets
+    uint32_t *gscan_status = nullptr;  // look-back words of the chunk scan
+    int64_t walk_grid = 0;             // resident walk blocks (persistent grid)
+    int walk_grid_key = -1;
+    uint32_t *gorder = nullptr;        // walk processing order of the groups
+    uint32_t *gkey = nullptr;          // per group: extent bucket (scratch for gorder)
+    uint32_t *gbucket = nullptr;       // [2][32] bucket counts / cursors
     int64_t groups_max = 0;
     // interaction lists (allocated on first use)
     int64_t *list_cnt = nullptr;       // [2][groups+1] counts -> offsets
     int32_t *pc_list = nullptr, *pp_list = nullptr;
     int64_t list_pc_cap = 0, list_pp_cap = 0, list_pc = 0, list_pp = 0;
     int64_t list_groups = -1;
+    int64_t list_groups_host = 0;      // group count used by the last list emission
     // direct-sum scratch
     double *direct_part = nullptr;
     size_t direct_part_bytes = 0;
@@ -251,6 +264,8 @@ cudaError_t launch_box_final(TreeWorkspace *ws, int nblocks, cudaStream_t s);
 cudaError_t launch_keys(TreeWorkspace *ws, const void *x, int64_t n, cudaStream_t s);
 cudaError_t launch_sort(TreeWorkspace *ws, int64_t n, cudaStream_t s);
 cudaError_t launch_octree(TreeWorkspace *ws, int64_t n, cudaStream_t s);
+// groups.cu
+cudaError_t launch_groups(TreeWorkspace *ws, int64_t n, cudaStream_t s);
 cudaError_t launch_gather(TreeWorkspace *ws, const void *x, const void *m, int64_t n, cudaStream_t s);
 cudaError_t launch_export_tree(TreeWorkspace *ws, int64_t nn, int32_t *level, uint32_t *corner, uint32_t *first,
                                uint32_t *count, int32_t *child, int32_t *nchild, cudaStream_t s);
@@ -276,4 +291,6 @@ cudaError_t launch_direct(TreeWorkspace *ws, const void *x, const void *m, int64
                           cudaStream_t s);
 cudaError_t launch_scan_lists(TreeWorkspace *ws, int64_t ngroups, cudaStream_t s);
 cudaError_t launch_gstat_reduce(TreeWorkspace *ws, int64_t ngroups, cudaStream_t s);
+cudaError_t launch_group_order(TreeWorkspace *ws, cudaStream_t s);
+cudaError_t launch_export_gstat(TreeWorkspace *ws, int64_t ngroups, uint32_t *out, cudaStream_t s);
 }  // namespace treegb

@@ -1,0 +1,117 @@
+// groups.cu -- walk groups from the sorted keys and the octree.
+//
+// Particles are taken in key order in chunks of Gs; a chunk is cut between
+// consecutive particles i-1, i that do not share the cell `delta` levels
+// above the finer of their two leaves:
+//   P(i-1, i) < max(leaf_level(i-1), leaf_level(i)) - delta,
+// P = number of leading octal digits the two keys share (21 if equal).
+// Neighbours in a group are then close on the scale of their own leaves, and
+// every group fits in the cell delta levels above its coarsest leaf.  This
+// keeps a chunk that jumps between distant parts of the Morton curve, or
+// from a dense region into a sparse one, from turning its walk into a
+// near-direct sum.  delta = 0 keeps plain chunks.
+// Output: gfirst[0..ng] (group g = sorted particles [gfirst[g], gfirst[g+1]))
+// and the group count in the counter block.
+#include "common.cuh"
+
+namespace treegb {
+
+constexpr int kGScanThreads = 256;
+constexpr int kGScanItems = 8;
+constexpr int kGScanTile = kGScanThreads * kGScanItems;
+
+// leaf level of every sorted particle
+__global__ void __launch_bounds__(256) k_leaf_levels(const uint32_t *__restrict__ ctr, const uint4 *__restrict__ ngeo,
+                                                     const uint2 *__restrict__ nlink, uint8_t *__restrict__ plev) {
+    const uint32_t nn = ctr[kCtrLevelStart + kLevels];
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nn; c += gridDim.x * blockDim.x) {
+        const uint4 g = ngeo[c];
+        if (!((g.w >> 8) & 1u)) continue;
+        const uint2 l = nlink[c];
+        const uint8_t lv = (uint8_t)(g.w & 0xffu);
+        for (uint32_t s = l.x; s < l.x + l.y; ++s) plev[s] = lv;
+    }
+}
+
+__device__ __forceinline__ bool group_starts(const uint64_t *__restrict__ skey, const uint8_t *__restrict__ plev,
+                                             int64_t i, int64_t s0, int delta) {
+    if (i == s0) return true;
+    if (delta <= 0) return false;
+    const uint64_t d = skey[i - 1] ^ skey[i];
+    const int shared = d ? (62 - (63 - __clzll((long long)d))) / 3 : kMaxLevel;
+    const int lmax = max((int)plev[i - 1], (int)plev[i]);
+    return shared < lmax - delta;
+}
+
+// One warp per chunk: number of groups that start inside it.
+template <bool WRITE>
+__global__ void __launch_bounds__(256) k_group_chunks(const uint64_t *__restrict__ skey, const uint8_t *__restrict__ plev,
+                                                      int64_t n, int gs, int delta, int64_t nchunks,
+                                                      uint32_t *__restrict__ ccount, const uint32_t *__restrict__ coff,
+                                                      uint32_t *__restrict__ gfirst, const uint32_t *__restrict__ ctr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (c >= nchunks) return;
+    const int64_t s0 = c * gs;
+    const int64_t s1 = min(n, s0 + gs);
+    uint32_t base = WRITE ? coff[c] : 0u;
+    uint32_t total = 0;
+    for (int64_t off = 0; off < gs; off += 32) {
+        const int64_t i = s0 + off + lane;
+        const bool st = off + lane < gs && i < s1 && group_starts(skey, plev, i, s0, delta);
+        const uint32_t b = __ballot_sync(0xffffffffu, st);
+        if (WRITE && st) gfirst[base + total + __popc(b & lanemask_lt())] = (uint32_t)i;
+        total += __popc(b);
+    }
+    if (!WRITE && lane == 0) ccount[c] = total;
+    if (WRITE && lane == 0 && c == nchunks - 1) gfirst[ctr[kCtrGroups]] = (uint32_t)n;
+}
+
+// Exclusive scan of ccount into coff (single pass, decoupled look-back);
+// the total is the group count.
+__global__ void __launch_bounds__(kGScanThreads) k_group_scan(const uint32_t *__restrict__ ccount,
+                                                              uint32_t *__restrict__ coff, int64_t nchunks,
+                                                              uint32_t *status, uint32_t *ctr, int32_t *dstatus) {
+    __shared__ uint32_t s_tile, s_excl, wt[32];
+    if (threadIdx.x == 0) s_tile = atomicAdd(ctr + kCtrGScanTicket, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t base = (int64_t)tile * kGScanTile + (int64_t)threadIdx.x * kGScanItems;
+    uint32_t v[kGScanItems], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kGScanItems; ++k) {
+        v[k] = base + k < nchunks ? ccount[base + k] : 0u;
+        sum += v[k];
+    }
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan(sum, wt, &tot);
+    if (threadIdx.x == 0) s_excl = lookback_single(status, tile, tot, dstatus);
+    __syncthreads();
+    uint32_t run = s_excl + ex;
+#pragma unroll
+    for (int k = 0; k < kGScanItems; ++k) {
+        if (base + k < nchunks) coff[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == kGScanThreads - 1 && (int64_t)(tile + 1) * kGScanTile >= nchunks) ctr[kCtrGroups] = run;
+}
+
+cudaError_t launch_groups(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
+    const int gs = ws->p.group_size;
+    const int64_t nchunks = (n + gs - 1) / gs;
+    const int64_t tiles = (nchunks + kGScanTile - 1) / kGScanTile;
+    cudaError_t e = cudaMemsetAsync(ws->gscan_status, 0, (size_t)tiles * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_leaf_levels<<<grid_for(ws->node_cap, 256, 152 * 8), 256, 0, s>>>(ws->ctr, ws->ngeo, ws->nlink, ws->plev);
+    const unsigned wb = (unsigned)((nchunks * 32 + 255) / 256);
+    k_group_chunks<false><<<wb, 256, 0, s>>>(ws->key, ws->plev, n, gs, ws->p.group_split, nchunks, ws->ccount,
+                                            nullptr, nullptr, ws->ctr);
+    k_group_scan<<<(unsigned)tiles, kGScanThreads, 0, s>>>(ws->ccount, ws->coff, nchunks, ws->gscan_status, ws->ctr,
+                                                          ws->dstatus);
+    k_group_chunks<true><<<wb, 256, 0, s>>>(ws->key, ws->plev, n, gs, ws->p.group_split, nchunks, nullptr, ws->coff,
+                                           ws->gfirst, ws->ctr);
+    ws->launches += 4;
+    return cudaGetLastError();
+}
+
+}  // namespace treegb

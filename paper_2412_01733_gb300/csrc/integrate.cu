@@ -232,6 +232,67 @@ cudaError_t launch_direct(TreeWorkspace *ws, const void *x, const void *m, int64
     return cudaGetLastError();
 }
 
+// ============================================================== walk order of the groups
+// Groups whose boxes are wide (sparse regions, or a run of the Morton curve
+// that jumps between distant cells) cost far more than the rest.  Walking
+// them first keeps them off the end of the launch.  Key: 21 - floor(log2 of
+// the box's largest side in grid units); a counting sort by key (the order
+// inside a key class is arbitrary; each group's result does not depend on it).
+__global__ void __launch_bounds__(256) k_group_key(const uint64_t *__restrict__ skey, const uint32_t *__restrict__ gfirst,
+                                                   const uint32_t *__restrict__ ctr, uint32_t *__restrict__ gkey,
+                                                   uint32_t *bucket) {
+    __shared__ uint32_t h[32];
+    if (threadIdx.x < 32) h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t ng = ctr[kCtrGroups];
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        const uint32_t s0 = gfirst[g], s1 = gfirst[g + 1];
+        uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0, 0, 0};
+        for (uint32_t i = s0; i < s1; ++i) {
+            const uint64_t k = skey[i];
+            const uint32_t q[3] = {compact3(k >> 2), compact3(k >> 1), compact3(k)};
+            for (int d = 0; d < 3; ++d) { lo[d] = min(lo[d], q[d]); hi[d] = max(hi[d], q[d]); }
+        }
+        const uint32_t e = max(hi[0] - lo[0], max(hi[1] - lo[1], hi[2] - lo[2]));
+        const uint32_t key = 21u - (31u - (uint32_t)__clz(e | 1u));
+        gkey[g] = key;
+        atomicAdd(&h[key], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(bucket + threadIdx.x, h[threadIdx.x]);
+}
+
+__global__ void k_group_scan(uint32_t *bucket) {
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int k = 0; k < 32; ++k) {
+            const uint32_t c = bucket[k];
+            bucket[32 + k] = s;
+            s += c;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_group_scatter(const uint32_t *__restrict__ gkey, const uint32_t *__restrict__ ctr,
+                                                       uint32_t *bucket, uint32_t *__restrict__ order) {
+    const uint32_t ng = ctr[kCtrGroups];
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        const uint32_t k = gkey[g];
+        order[atomicAdd(bucket + 32 + k, 1u)] = (uint32_t)g;
+    }
+}
+
+cudaError_t launch_group_order(TreeWorkspace *ws, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(ws->gbucket, 0, 64 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const int nb = grid_for(ws->n / 8 + 1, 256, 152 * 8);
+    k_group_key<<<nb, 256, 0, s>>>(ws->key, ws->gfirst, ws->ctr, ws->gkey, ws->gbucket);
+    k_group_scan<<<1, 32, 0, s>>>(ws->gbucket);
+    k_group_scatter<<<nb, 256, 0, s>>>(ws->gkey, ws->ctr, ws->gbucket, ws->gorder);
+    ws->launches += 3;
+    return cudaGetLastError();
+}
+
 // ============================================================== direct sum without allocation
 // tree_direct_forces needs a workspace, and the workspace allocates its
 // scratch with cudaMalloc.  Callers that must not allocate device memory
@@ -270,13 +331,13 @@ cudaError_t noalloc_scratch(double **out) {
 // ============================================================== per-group walk records
 // gstat[g] = {n_pc cells, n_pp particles, max stack, n_pp leaves}.
 // Pair totals: sum_g |g| n_pc and sum_g |g| n_pp; deepest stack.
-__global__ void __launch_bounds__(256) k_gstat_reduce(const uint4 *__restrict__ gstat, int64_t ng, int64_t n,
-                                                      int gs, unsigned long long *stats) {
+__global__ void __launch_bounds__(256) k_gstat_reduce(const uint4 *__restrict__ gstat, const uint32_t *__restrict__ gfirst,
+                                                      const uint32_t *__restrict__ ctr, unsigned long long *stats) {
     unsigned long long pp = 0, pc = 0, ms = 0;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t ng = ctr[kCtrGroups];
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
         const uint4 r = gstat[g];
-        const int64_t rem = n - g * gs;
-        const unsigned long long c = (unsigned long long)(rem < gs ? rem : gs);
+        const unsigned long long c = (unsigned long long)(gfirst[g + 1] - gfirst[g]);
         pc += c * r.x;
         pp += c * r.y;
         ms = ms > r.z ? ms : r.z;
@@ -339,6 +400,20 @@ __global__ void __launch_bounds__(1024) k_list_scan(const uint4 *__restrict__ gs
     if (tid < 2) off[tid * (ng + 1) + ng] = (int64_t)carry[tid];
 }
 
+__global__ void k_export_gstat(const uint4 *__restrict__ gstat, int64_t ng, uint32_t *__restrict__ out) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 r = gstat[g];
+        out[g] = r.x; out[ng + g] = r.y; out[2 * ng + g] = r.z; out[3 * ng + g] = r.w;
+    }
+}
+
+cudaError_t launch_export_gstat(TreeWorkspace *ws, int64_t ngroups, uint32_t *out, cudaStream_t s) {
+    if (ngroups <= 0) return cudaSuccess;
+    k_export_gstat<<<grid_for(ngroups, 256, 152 * 8), 256, 0, s>>>(ws->gstat, ngroups, out);
+    ws->launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scan_lists(TreeWorkspace *ws, int64_t ngroups, cudaStream_t s) {
     k_list_scan<<<1, 1024, 0, s>>>(ws->gstat, ngroups, ws->list_cnt);
     ws->launches += 1;
@@ -348,8 +423,7 @@ cudaError_t launch_scan_lists(TreeWorkspace *ws, int64_t ngroups, cudaStream_t s
 cudaError_t launch_gstat_reduce(TreeWorkspace *ws, int64_t ngroups, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(ws->stats, 0, kStatCount * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    k_gstat_reduce<<<grid_for(ngroups, 256, 152 * 4), 256, 0, s>>>(ws->gstat, ngroups, ws->n, ws->p.group_size,
-                                                                    ws->stats);
+    k_gstat_reduce<<<grid_for(ngroups, 256, 152 * 4), 256, 0, s>>>(ws->gstat, ws->gfirst, ws->ctr, ws->stats);
     ws->launches += 1;
     return cudaGetLastError();
 }

@@ -47,18 +47,28 @@ struct WalkArgs {
     int32_t *dstatus;
     const int64_t *list_off;  // [2][ngroups+1] (emit mode)
     int32_t *pc_list, *pp_list;
+    const uint32_t *order;    // processing order of the groups (widest boxes first), or NULL
+    const uint32_t *gfirst;   // group g = sorted particles [gfirst[g], gfirst[g+1])
+    uint32_t *ctr;            // counter block: group count and the walk's group ticket
 };
 
 template <typename Real> __device__ __forceinline__ Real rsqrt_r(Real x);
 template <> __device__ __forceinline__ float rsqrt_r<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_r<double>(double x) { return rsqrt(x); }
 
+// Source staging per warp: FP32 uses 16 source pairs x 5 float4 (pair-
+// interleaved, see pp_pair / pc_pair); FP64 uses 32 x (double4, double4, double2).
+template <typename Real>
+__host__ __device__ constexpr size_t walk_stage_bytes() {
+    return sizeof(Real) == 4 ? 80 * sizeof(float4)
+                             : 32 * (sizeof(typename Vec4<Real>::T) * 2 + sizeof(typename Vec2<Real>::T));
+}
+
 // Per-warp shared-memory slice, rounded up to 32 bytes so that every warp's
 // staging arrays (float4 / 32-byte double4) stay aligned.
 template <typename Real>
 __host__ __device__ constexpr size_t walk_warp_bytes(int stack_depth) {
-    return (((size_t)(stack_depth + kPPCap + kPCCap + 32) * 4 +
-             32 * (sizeof(typename Vec4<Real>::T) * 2 + sizeof(typename Vec2<Real>::T))) + 31) & ~(size_t)31;
+    return (((size_t)(stack_depth + kPPCap + kPCCap + 32) * 4 + walk_stage_bytes<Real>()) + 31) & ~(size_t)31;
 }
 
 // --- pair terms ------------------------------------------------------------
@@ -114,6 +124,73 @@ __device__ __forceinline__ void pc_term(Real px, Real py, Real pz, const typenam
     }
 }
 
+// --- packed FP32 pair terms: two sources per instruction ---------------------
+// Each float2 holds one quantity of two sources (or two cells); the target is
+// held negated and duplicated, nP = (-p, -p), so every difference is an add.
+// PP: d = r_s - r_i, accumulates m d / r^3 and -m / r for both sources.
+template <bool SOFT>
+__device__ __forceinline__ void pp_pair(float2 nx, float2 ny, float2 nz, float2 X, float2 Y, float2 Z, float2 M,
+                                        float2 eps2, float2 neg1, float2 (&acc)[4]) {
+    const float2 dx = __fadd2_rn(X, nx), dy = __fadd2_rn(Y, ny), dz = __fadd2_rn(Z, nz);
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
+    float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    if (!SOFT) {
+        ri.x = r2.x > 0.f ? ri.x : 0.f;
+        ri.y = r2.y > 0.f ? ri.y : 0.f;
+    }
+    const float2 ri2 = __fmul2_rn(ri, ri);
+    const float2 mr = __fmul2_rn(M, ri);
+    const float2 mr3 = __fmul2_rn(mr, ri2);
+    acc[0] = __ffma2_rn(mr3, dx, acc[0]);
+    acc[1] = __ffma2_rn(mr3, dy, acc[1]);
+    acc[2] = __ffma2_rn(mr3, dz, acc[2]);
+    acc[3] = __ffma2_rn(neg1, mr, acc[3]);
+}
+
+// PC for two cells.  With u = R - r_i (= -y) and the staged negated
+// quadrupole Qn = -Q, w = Qn u equals Q y, u.w = -(y.Q.y), and the terms of
+// pc_term become a = [M/r^3 - 5/2 (u.w)/r^7] u + w/r^5, phi = -M/r + 1/2 (u.w)/r^5.
+template <bool QUAD, bool SOFT>
+__device__ __forceinline__ void pc_pair(float2 nx, float2 ny, float2 nz, const float4 &A, const float4 &B,
+                                        const float4 &C, const float4 &D, const float4 &E, float2 eps2,
+                                        float2 neg1, float2 half, float2 m25, float2 (&acc)[4]) {
+    const float2 ux = __fadd2_rn(make_float2(A.x, A.y), nx);
+    const float2 uy = __fadd2_rn(make_float2(A.z, A.w), ny);
+    const float2 uz = __fadd2_rn(make_float2(B.x, B.y), nz);
+    const float2 M = make_float2(B.z, B.w);
+    const float2 r2 = __ffma2_rn(ux, ux, __ffma2_rn(uy, uy, __ffma2_rn(uz, uz, eps2)));
+    float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    if (!SOFT) {
+        ri.x = r2.x > 0.f ? ri.x : 0.f;
+        ri.y = r2.y > 0.f ? ri.y : 0.f;
+    }
+    const float2 ri2 = __fmul2_rn(ri, ri);
+    const float2 Mr = __fmul2_rn(M, ri);
+    const float2 Mr3 = __fmul2_rn(Mr, ri2);
+    if (QUAD) {
+        const float2 qxx = make_float2(C.x, C.y), qyy = make_float2(C.z, C.w);
+        const float2 qzz = make_float2(D.x, D.y), qxy = make_float2(D.z, D.w);
+        const float2 qxz = make_float2(E.x, E.y), qyz = make_float2(E.z, E.w);
+        const float2 wx = __ffma2_rn(qxx, ux, __ffma2_rn(qxy, uy, __fmul2_rn(qxz, uz)));
+        const float2 wy = __ffma2_rn(qxy, ux, __ffma2_rn(qyy, uy, __fmul2_rn(qyz, uz)));
+        const float2 wz = __ffma2_rn(qxz, ux, __ffma2_rn(qyz, uy, __fmul2_rn(qzz, uz)));
+        const float2 uw = __ffma2_rn(ux, wx, __ffma2_rn(uy, wy, __fmul2_rn(uz, wz)));
+        const float2 r3 = __fmul2_rn(ri, ri2);
+        const float2 r5 = __fmul2_rn(r3, ri2);
+        const float2 t = __fmul2_rn(uw, r5);
+        const float2 c = __ffma2_rn(t, __fmul2_rn(ri2, m25), Mr3);
+        acc[0] = __ffma2_rn(c, ux, __ffma2_rn(r5, wx, acc[0]));
+        acc[1] = __ffma2_rn(c, uy, __ffma2_rn(r5, wy, acc[1]));
+        acc[2] = __ffma2_rn(c, uz, __ffma2_rn(r5, wz, acc[2]));
+        acc[3] = __ffma2_rn(neg1, Mr, __ffma2_rn(half, t, acc[3]));
+    } else {
+        acc[0] = __ffma2_rn(Mr3, ux, acc[0]);
+        acc[1] = __ffma2_rn(Mr3, uy, acc[1]);
+        acc[2] = __ffma2_rn(Mr3, uz, acc[2]);
+        acc[3] = __ffma2_rn(neg1, Mr, acc[3]);
+    }
+}
+
 template <typename Real, bool KAHAN>
 __device__ __forceinline__ void fold(Real (&sum)[4], Real (&cmp)[4], const Real (&part)[4]) {
 #pragma unroll
@@ -139,7 +216,7 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 }
 
 template <typename Real, int TPL, bool QUAD, bool KAHAN, bool SOFT, int MODE>
-__global__ void __launch_bounds__(kWalkWarps * 32, 5) k_walk(const WalkArgs A) {
+__global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(const WalkArgs A) {
     using V4 = typename Vec4<Real>::T;
     using V2 = typename Vec2<Real>::T;
     extern __shared__ __align__(32) unsigned char smem[];
@@ -150,10 +227,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 5) k_walk(const WalkArgs A) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int SD = A.stack_depth;
     unsigned char *wb = smem + (size_t)warp * walk_warp_bytes<Real>(SD);
-    V4 *stA = reinterpret_cast<V4 *>(wb);
+    V4 *stA = reinterpret_cast<V4 *>(wb);            // FP64 layout
     V4 *stB = stA + 32;
     V2 *stC = reinterpret_cast<V2 *>(stB + 32);
-    uint32_t *stack = reinterpret_cast<uint32_t *>(stC + 32);
+    float4 *stF = reinterpret_cast<float4 *>(wb);    // FP32 pair-interleaved layout
+    uint32_t *stack = reinterpret_cast<uint32_t *>(wb + walk_stage_bytes<Real>());
     uint32_t *ppbuf = stack + SD;
     uint32_t *pcbuf = ppbuf + kPPCap;
     int *mark = reinterpret_cast<int *>(pcbuf + kPCCap);
@@ -165,11 +243,16 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 5) k_walk(const WalkArgs A) {
     const V2 *__restrict__ momC = reinterpret_cast<const V2 *>(A.mom_c);
     const Real eps2 = (Real)A.eps2;
 
-    const int64_t g = (int64_t)blockIdx.x * kWalkWarps + warp;
-    if (g >= A.ngroups) return;
-    const int64_t s0 = g * A.gs;
-    const int64_t rem = A.n - s0;
-    const int cnt = rem < A.gs ? (int)rem : A.gs;
+    // persistent warps: each takes the next group slot until all are done
+    const uint32_t ngroups = A.ctr[kCtrGroups];
+    for (;;) {
+    uint32_t slot = 0;
+    if (lane == 0) slot = atomicAdd(A.ctr + kCtrWalkTicket, 1u);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (slot >= ngroups) break;
+    const int64_t g = A.order ? (int64_t)A.order[slot] : (int64_t)slot;
+    const int64_t s0 = A.gfirst[g];
+    const int cnt = (int)(A.gfirst[g + 1] - A.gfirst[g]);
 
     // targets and the group's integer box
     Real px[TPL], py[TPL], pz[TPL], pm[TPL];
@@ -199,72 +282,172 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 5) k_walk(const WalkArgs A) {
         for (int c = 0; c < 4; ++c) { sum[t][c] = Real(0); cmp[t][c] = Real(0); }
 
     // --- evaluation helpers (whole warp) ---
-    auto eval_pp_stage = [&](int ns) {
-        // sources already in stA[0..ns)
-        Real part[TPL][4];
+    // FP32: sources are staged as pairs, pair k in stF[5k .. 5k+4]:
+    //   PP: (x0, x1, y0, y1), (z0, z1, m0, m1)
+    //   PC: (Rx0, Rx1, Ry0, Ry1), (Rz0, Rz1, M0, M1), -(Qxx, Qyy), -(Qzz, Qxy), -(Qxz, Qyz)
+    // with an odd count padded by a massless source at the origin.
+    float2 nX[TPL], nY[TPL], nZ[TPL];
 #pragma unroll
-        for (int t = 0; t < TPL; ++t)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) part[t][c] = Real(0);
-        if (ns == 32) {
-#pragma unroll 8
-            for (int j = 0; j < 32; ++j) {
-                const V4 s = stA[j];
-#pragma unroll
-                for (int t = 0; t < TPL; ++t) pp_term<Real, SOFT>(px[t], py[t], pz[t], s, eps2, part[t]);
+    for (int t = 0; t < TPL; ++t) {
+        nX[t] = make_float2(-(float)px[t], -(float)px[t]);
+        nY[t] = make_float2(-(float)py[t], -(float)py[t]);
+        nZ[t] = make_float2(-(float)pz[t], -(float)pz[t]);
+    }
+    const float2 eps2v = make_float2((float)A.eps2, (float)A.eps2);
+    const float2 neg1 = make_float2(-1.f, -1.f), halfv = make_float2(0.5f, 0.5f), m25 = make_float2(-2.5f, -2.5f);
+
+    auto stage_pp = [&](const V4 &src, int ns) {
+        if constexpr (sizeof(Real) == 4) {
+            const int ne = (ns + 1) & ~1;
+            if (lane < ne) {
+                float *a = reinterpret_cast<float *>(stF + 5 * (lane >> 1));
+                const int sl = lane & 1;
+                const bool v = lane < ns;
+                a[sl] = v ? (float)src.x : 0.f;
+                a[2 + sl] = v ? (float)src.y : 0.f;
+                a[4 + sl] = v ? (float)src.z : 0.f;
+                a[6 + sl] = v ? (float)src.w : 0.f;
             }
         } else {
+            if (lane < ns) stA[lane] = src;
+        }
+    };
+    auto eval_pp_stage = [&](int ns) {
+        if constexpr (sizeof(Real) == 4) {
+            float2 part[TPL][4];
+#pragma unroll
+            for (int t = 0; t < TPL; ++t)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) part[t][c] = make_float2(0.f, 0.f);
+            const int np = (ns + 1) >> 1;
+            if (np == 16) {
+#pragma unroll 4
+                for (int k = 0; k < 16; ++k) {
+                    const float4 a = stF[5 * k], b = stF[5 * k + 1];
+#pragma unroll
+                    for (int t = 0; t < TPL; ++t)
+                        pp_pair<SOFT>(nX[t], nY[t], nZ[t], make_float2(a.x, a.y), make_float2(a.z, a.w),
+                                      make_float2(b.x, b.y), make_float2(b.z, b.w), eps2v, neg1, part[t]);
+                }
+            } else {
+                for (int k = 0; k < np; ++k) {
+                    const float4 a = stF[5 * k], b = stF[5 * k + 1];
+#pragma unroll
+                    for (int t = 0; t < TPL; ++t)
+                        pp_pair<SOFT>(nX[t], nY[t], nZ[t], make_float2(a.x, a.y), make_float2(a.z, a.w),
+                                      make_float2(b.x, b.y), make_float2(b.z, b.w), eps2v, neg1, part[t]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < TPL; ++t) {
+                Real p1[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) p1[c] = (Real)(part[t][c].x + part[t][c].y);
+                fold<Real, KAHAN>(sum[t], cmp[t], p1);
+            }
+        } else {
+            Real part[TPL][4];
+#pragma unroll
+            for (int t = 0; t < TPL; ++t)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) part[t][c] = Real(0);
             for (int j = 0; j < ns; ++j) {
                 const V4 s = stA[j];
 #pragma unroll
                 for (int t = 0; t < TPL; ++t) pp_term<Real, SOFT>(px[t], py[t], pz[t], s, eps2, part[t]);
             }
-        }
 #pragma unroll
-        for (int t = 0; t < TPL; ++t) fold<Real, KAHAN>(sum[t], cmp[t], part[t]);
+            for (int t = 0; t < TPL; ++t) fold<Real, KAHAN>(sum[t], cmp[t], part[t]);
+        }
     };
     auto eval_pp_list = [&](const uint32_t *buf, int ns) {
-        V4 s;
+        V4 s{};
         if (lane < ns) s = spos[buf[lane]];
         __syncwarp();
-        if (lane < ns) stA[lane] = s;
+        stage_pp(s, ns);
         __syncwarp();
         eval_pp_stage(ns);
         __syncwarp();
     };
     auto eval_pp_range = [&](uint32_t first, int ns) {
-        V4 s;
+        V4 s{};
         if (lane < ns) s = spos[first + lane];
         __syncwarp();
-        if (lane < ns) stA[lane] = s;
+        stage_pp(s, ns);
         __syncwarp();
         eval_pp_stage(ns);
         __syncwarp();
     };
     auto eval_pc_list = [&](const uint32_t *buf, int ns) {
-        if (lane < ns) {
-            const uint32_t c = buf[lane];
-            stA[lane] = momA[c];
-            if (QUAD) { stB[lane] = momB[c]; stC[lane] = momC[c]; }
-        }
-        __syncwarp();
-        Real part[TPL][4];
-#pragma unroll
-        for (int t = 0; t < TPL; ++t)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) part[t][c] = Real(0);
-        V4 b0{};
-        V2 c0{};
-        if (ns == 32) {
-#pragma unroll 4
-            for (int j = 0; j < 32; ++j) {
-                const V4 a = stA[j];
-                const V4 b = QUAD ? stB[j] : b0;
-                const V2 c = QUAD ? stC[j] : c0;
-#pragma unroll
-                for (int t = 0; t < TPL; ++t) pc_term<Real, QUAD, SOFT>(px[t], py[t], pz[t], a, b, c, eps2, part[t]);
+        if constexpr (sizeof(Real) == 4) {
+            const int ne = (ns + 1) & ~1;
+            if (lane < ne) {
+                float *q = reinterpret_cast<float *>(stF + 5 * (lane >> 1));
+                const int sl = lane & 1;
+                V4 a{};
+                V4 b{};
+                V2 c{};
+                if (lane < ns) {
+                    const uint32_t cell = buf[lane];
+                    a = momA[cell];
+                    if (QUAD) { b = momB[cell]; c = momC[cell]; }
+                }
+                q[sl] = a.x; q[2 + sl] = a.y; q[4 + sl] = a.z; q[6 + sl] = a.w;
+                if (QUAD) {
+                    q[8 + sl] = -b.x; q[10 + sl] = -b.y; q[12 + sl] = -b.z; q[14 + sl] = -b.w;
+                    q[16 + sl] = -c.x; q[18 + sl] = -c.y;
+                }
             }
+            __syncwarp();
+            float2 part[TPL][4];
+#pragma unroll
+            for (int t = 0; t < TPL; ++t)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) part[t][c] = make_float2(0.f, 0.f);
+            const int np = (ns + 1) >> 1;
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (np == 16) {
+#pragma unroll 2
+                for (int k = 0; k < 16; ++k) {
+                    const float4 a = stF[5 * k], b = stF[5 * k + 1];
+                    const float4 c = QUAD ? stF[5 * k + 2] : z4, d = QUAD ? stF[5 * k + 3] : z4,
+                                 e = QUAD ? stF[5 * k + 4] : z4;
+#pragma unroll
+                    for (int t = 0; t < TPL; ++t)
+                        pc_pair<QUAD, SOFT>(nX[t], nY[t], nZ[t], a, b, c, d, e, eps2v, neg1, halfv, m25, part[t]);
+                }
+            } else {
+                for (int k = 0; k < np; ++k) {
+                    const float4 a = stF[5 * k], b = stF[5 * k + 1];
+                    const float4 c = QUAD ? stF[5 * k + 2] : z4, d = QUAD ? stF[5 * k + 3] : z4,
+                                 e = QUAD ? stF[5 * k + 4] : z4;
+#pragma unroll
+                    for (int t = 0; t < TPL; ++t)
+                        pc_pair<QUAD, SOFT>(nX[t], nY[t], nZ[t], a, b, c, d, e, eps2v, neg1, halfv, m25, part[t]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < TPL; ++t) {
+                Real p1[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) p1[c] = (Real)(part[t][c].x + part[t][c].y);
+                fold<Real, KAHAN>(sum[t], cmp[t], p1);
+            }
+            __syncwarp();
         } else {
+            if (lane < ns) {
+                const uint32_t c = buf[lane];
+                stA[lane] = momA[c];
+                if (QUAD) { stB[lane] = momB[c]; stC[lane] = momC[c]; }
+            }
+            __syncwarp();
+            Real part[TPL][4];
+#pragma unroll
+            for (int t = 0; t < TPL; ++t)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) part[t][c] = Real(0);
+            V4 b0{};
+            V2 c0{};
             for (int j = 0; j < ns; ++j) {
                 const V4 a = stA[j];
                 const V4 b = QUAD ? stB[j] : b0;
@@ -272,10 +455,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 5) k_walk(const WalkArgs A) {
 #pragma unroll
                 for (int t = 0; t < TPL; ++t) pc_term<Real, QUAD, SOFT>(px[t], py[t], pz[t], a, b, c, eps2, part[t]);
             }
-        }
 #pragma unroll
-        for (int t = 0; t < TPL; ++t) fold<Real, KAHAN>(sum[t], cmp[t], part[t]);
-        __syncwarp();
+            for (int t = 0; t < TPL; ++t) fold<Real, KAHAN>(sum[t], cmp[t], part[t]);
+            __syncwarp();
+        }
     };
 
     // --- traversal ---
@@ -447,6 +630,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 5) k_walk(const WalkArgs A) {
             }
         }
     }
+    }  // group loop
 }
 
 }  // namespace treegb
@@ -458,7 +642,7 @@ inline WalkArgs make_walk_args(TreeWorkspace *ws, const WalkOut &out) {
     WalkArgs a;
     a.n = ws->n;
     a.gs = ws->p.group_size;
-    a.ngroups = (ws->n + ws->p.group_size - 1) / ws->p.group_size;
+    a.ngroups = ws->list_groups_host;  // host copy of the group count (list emission only)
     a.spos = ws->spos;
     a.skey = ws->key;
     a.perm = ws->idx;
@@ -481,18 +665,32 @@ inline WalkArgs make_walk_args(TreeWorkspace *ws, const WalkOut &out) {
     a.list_off = ws->list_cnt;
     a.pc_list = ws->pc_list;
     a.pp_list = ws->pp_list;
+    a.order = ws->gorder;
+    a.gfirst = ws->gfirst;
+    a.ctr = ws->ctr;
     return a;
 }
 
 template <typename Real, int TPL, bool QUAD, bool KAHAN, bool SOFT, int MODE>
 cudaError_t walk_run(TreeWorkspace *ws, const WalkArgs &a, cudaStream_t s) {
-    if (a.ngroups <= 0) return cudaSuccess;
+    if (ws->n <= 0) return cudaSuccess;
     auto k = k_walk<Real, TPL, QUAD, KAHAN, SOFT, MODE>;
     const size_t smem = kWalkWarps * walk_warp_bytes<Real>(a.stack_depth);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const unsigned nb = (unsigned)((a.ngroups + kWalkWarps - 1) / kWalkWarps);
-    k<<<nb, kWalkWarps * 32, smem, s>>>(a);
+    // persistent grid: the resident blocks, never more than the groups need
+    int per_sm = 0, sms = 0, dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWalkWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t ng_bound = (ws->n + kWalkWarps - 1) / kWalkWarps;
+    int64_t nb = (int64_t)(per_sm > 0 ? per_sm : 1) * sms;
+    if (nb > ng_bound) nb = ng_bound;
+    if (nb < 1) nb = 1;
+    e = cudaMemsetAsync(ws->ctr + kCtrWalkTicket, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k<<<(unsigned)nb, kWalkWarps * 32, smem, s>>>(a);
     ws->launches += 1;
     return cudaGetLastError();
 }

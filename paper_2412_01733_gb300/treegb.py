@@ -27,7 +27,7 @@ class TreeParams(ctypes.Structure):
     _fields_ = [("G", ctypes.c_double), ("eps", ctypes.c_double), ("theta", ctypes.c_double),
                 ("order", ctypes.c_int32), ("leaf_cap", ctypes.c_int32), ("group_size", ctypes.c_int32),
                 ("stack_depth", ctypes.c_int32), ("precision", ctypes.c_int32), ("kahan", ctypes.c_int32),
-                ("node_cap", ctypes.c_int64)]
+                ("group_split", ctypes.c_int32), ("node_cap", ctypes.c_int64)]
 
 
 class TreeInfo(ctypes.Structure):
@@ -65,6 +65,8 @@ _SIGNATURES = {
     "tree_export_tree": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "tree_export_moments": [_vp, _vp, _vp, _vp, _vp],
     "tree_export_lists": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "tree_export_group_stats": [_vp, _vp, _vp],
+    "tree_export_groups": [_vp, _vp, _vp],
     "tree_mac_table": [_dbl, ctypes.POINTER(_i64)],
     "tree_direct_forces_noalloc": [_vp, _vp, _i64, _i32, _dbl, _dbl, _vp, _i64, _vp, _vp, _vp],
     "tree_timing_enable": [_vp, _i32],
@@ -322,6 +324,21 @@ class Workspace:
         Q = torch.empty((6, nn), dtype=torch.float64, device="cuda")
         _check("tree_export_moments", lib().tree_export_moments(self._h, _ptr(M), _ptr(R), _ptr(Q), _stream()))
         return M, R, Q
+
+    def export_group_stats(self):
+        """Per-group records of the last walk: int64 CUDA tensor (4, n_groups) =
+        (far cells, near particles, deepest stack, near leaves)."""
+        ng = self.info()["n_groups"]
+        out = torch.empty((4, max(ng, 1)), dtype=torch.int32, device="cuda")
+        _check("tree_export_group_stats", lib().tree_export_group_stats(self._h, _ptr(out), _stream()))
+        return out[:, :ng].long()
+
+    def export_groups(self):
+        """Walk groups of the last build: int64 CUDA tensor of n_groups + 1 first indices."""
+        ng = self.info()["n_groups"]
+        out = torch.empty(ng + 1, dtype=torch.int32, device="cuda")
+        _check("tree_export_groups", lib().tree_export_groups(self._h, _ptr(out), _stream()))
+        return out.long()
 
     def export_lists(self):
         inf = self.info()

@@ -73,6 +73,8 @@ def _check_structure(orc, ws, xg, mg, ref, gs):
     np.testing.assert_allclose(M, ref.M, rtol=1e-12, atol=0)
     assert np.all(np.abs(R - ref.R) <= 1e-12 * np.ldexp(1.0, ref.k))
     assert np.all(np.abs(Q - ref.Q) <= 1e-10 * (np.abs(ref.M) * side * side + 1e-300))
+    # walk groups
+    np.testing.assert_array_equal(ws.export_groups().cpu().numpy(), ref.gfirst)
     # lists, as sets per group
     pc_off, pc, pp_off, pp = (v.cpu().numpy() for v in ws.export_lists())
     np.testing.assert_array_equal(pc_off, ref.pc_off)
@@ -87,6 +89,10 @@ CASES = [
     ("plummer50001_quad_g64", "plummer", 50001, dict(eps=0.005, theta=0.5, order=2, leaf_cap=8, group_size=64)),
     ("galaxy30k_quad", "galaxy", 30000, dict(eps=0.02, theta=0.7, order=2, leaf_cap=16, group_size=32)),
     ("plummer3k_lcap1_g16", "plummer", 3001, dict(eps=0.01, theta=1.0, order=2, leaf_cap=1, group_size=16)),
+    ("galaxy20k_chunks", "galaxy", 20000, dict(eps=0.02, theta=0.7, order=2, leaf_cap=16, group_size=32,
+                                               group_split=0)),
+    ("galaxy20k_split1_g64", "galaxy", 20011, dict(eps=0.02, theta=0.6, order=2, leaf_cap=8, group_size=64,
+                                                   group_split=1)),
 ]
 
 
@@ -104,7 +110,7 @@ def test_fp32_parity(orc, name, kind, n, p):
     ws, xg, mg, a, phi = _run(x, m, **p)
     assert ws.status() == 0
     ref = orc.tree_forces(_np64(xg), _np64(mg), eps=p["eps"], theta=p["theta"], lcap=p["leaf_cap"],
-                          gs=p["group_size"], quad=p["order"] == 2)
+                          gs=p["group_size"], quad=p["order"] == 2, delta=p.get("group_split", 3))
     _check_structure(orc, ws, xg, mg, ref, p["group_size"])
     e = _rel_err(_np64(a), ref.a)
     assert np.median(e) <= 1e-5, np.median(e)
@@ -113,8 +119,7 @@ def test_fp32_parity(orc, name, kind, n, p):
     assert np.median(ep) <= 1e-5 and ep.max() <= 1e-4
     inf = ws.info()
     # interaction counts agree with the oracle's lists
-    gs = p["group_size"]
-    sizes = np.minimum(gs, n - gs * np.arange(len(ref.pc_off) - 1))
+    sizes = np.diff(ref.gfirst)
     assert inf["pc_pairs"] == int((sizes * np.diff(ref.pc_off)).sum())
     leaf_pp = np.zeros(len(ref.pp_off) - 1, np.int64)
     np.add.at(leaf_pp, np.repeat(np.arange(len(leaf_pp)), np.diff(ref.pp_off)), ref.tree.count[ref.pp_list])
@@ -127,7 +132,7 @@ def test_fp64_parity(orc, name, kind, n, p):
     ws, xg, mg, a, phi = _run(x, m, precision="f64", **p)
     assert ws.status() == 0
     ref = orc.tree_forces(_np64(xg), _np64(mg), eps=p["eps"], theta=p["theta"], lcap=p["leaf_cap"],
-                          gs=p["group_size"], quad=p["order"] == 2)
+                          gs=p["group_size"], quad=p["order"] == 2, delta=p.get("group_split", 3))
     _check_structure(orc, ws, xg, mg, ref, p["group_size"])
     e = _rel_err(_np64(a), ref.a)
     assert e.max() <= 1e-11, e.max()

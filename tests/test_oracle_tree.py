@@ -159,22 +159,23 @@ def test_moments_parallel_axis(orc):
 
 
 # ---------------------------------------------------------------- lists
-def _check_lists(orc, x, theta, gs, lcap):
+def _check_lists(orc, x, theta, gs, lcap, delta=3):
     lo, k = orc.box(x)
     q, key = orc.keys(x, lo, k)
     perm = orc.sort(key)
     t = orc.octree(key[perm], lcap)
     qs = q[:, perm]
-    pc_off, pc, pp_off, pp = orc.lists(qs, gs, theta, t)
+    gf = orc.groups(key[perm], t, gs, delta)
+    pc_off, pc, pp_off, pp = orc.lists(qs, gf, theta, t)
     n = x.shape[1]
-    ng = (n + gs - 1) // gs
+    ng = len(gf) - 1
     parent = np.full(t.nn, -1)
     for c in range(t.nn):
         if t.nchild[c]:
             parent[t.child[c]: t.child[c] + t.nchild[c]] = c
     th2 = theta * theta
     for g in range(ng):
-        s0, s1 = g * gs, min(n, (g + 1) * gs)
+        s0, s1 = gf[g], gf[g + 1]
         glo = qs[:, s0:s1].min(axis=1).astype(np.int64)
         ghi = qs[:, s0:s1].max(axis=1).astype(np.int64) + 1
 
@@ -204,12 +205,61 @@ def _check_lists(orc, x, theta, gs, lcap):
     return pc_off, pp_off
 
 
-@pytest.mark.parametrize("theta,gs,lcap", [(0.7, 32, 16), (1.0, 16, 4), (0.4, 64, 1), (0.0, 32, 8)])
-def test_lists_partition_and_criterion(orc, theta, gs, lcap):
+@pytest.mark.parametrize("theta,gs,lcap,delta", [(0.7, 32, 16, 3), (1.0, 16, 4, 2), (0.4, 64, 1, 1),
+                                                (0.0, 32, 8, 2), (0.7, 32, 16, 0)])
+def test_lists_partition_and_criterion(orc, theta, gs, lcap, delta):
     x, _, _ = inputs.plummer(700, 13)
-    pc_off, pp_off = _check_lists(orc, x.numpy(), theta, gs, lcap)
+    pc_off, pp_off = _check_lists(orc, x.numpy(), theta, gs, lcap, delta)
     if theta == 0.0:
         assert pc_off[-1] == 0
+
+
+def _octal_digits(key):
+    """The 21 octal digits of a 63-bit key, most significant first."""
+    return [(int(key) >> (3 * (20 - i))) & 7 for i in range(21)]
+
+
+@pytest.mark.parametrize("kind,n,gs,lcap,delta", [("plummer", 3000, 32, 16, 3), ("galaxy", 4000, 32, 8, 2),
+                                                  ("galaxy", 2000, 64, 4, 1), ("plummer", 1000, 16, 1, 3),
+                                                  ("plummer", 500, 32, 16, 0)])
+def test_groups_rule(orc, kind, n, gs, lcap, delta):
+    """Walk groups: chunks of gs in key order, cut between neighbours that do
+    not share the cell delta levels above the finer of their leaves.
+    Checked by counting shared octal digits directly, with leaf levels from
+    a scan of the leaves, and through the box bound the rule implies."""
+    x, _, _ = (inputs.plummer if kind == "plummer" else inputs.galaxy)(n, 29)
+    x = x.numpy()
+    lo, k = orc.box(x)
+    q, key = orc.keys(x, lo, k)
+    perm = orc.sort(key)
+    sk = key[perm]
+    t = orc.octree(sk, lcap)
+    gf = orc.groups(sk, t, gs, delta)
+    leaf_level = np.full(n, -1)
+    for c in np.nonzero(t.nchild == 0)[0]:
+        leaf_level[t.first[c]: t.first[c] + t.count[c]] = t.level[c]
+    assert np.all(leaf_level >= 0)
+    want = [0]
+    digits = [_octal_digits(v) for v in sk]
+    for i in range(1, n):
+        shared = 21
+        for j in range(21):
+            if digits[i][j] != digits[i - 1][j]:
+                shared = j
+                break
+        if i % gs == 0 or (delta > 0 and shared < max(leaf_level[i], leaf_level[i - 1]) - delta):
+            want.append(i)
+    np.testing.assert_array_equal(gf, want + [n])
+    sizes = np.diff(gf)
+    assert sizes.min() >= 1 and sizes.max() <= gs
+    if delta == 0:
+        assert len(gf) - 1 == (n + gs - 1) // gs
+    qs = q[:, perm]
+    for g in range(len(gf) - 1):
+        a, b = gf[g], gf[g + 1]
+        lvl = max(0, leaf_level[a:b].min() - delta) if delta > 0 else 0
+        cell = (qs[:, a:b] >> (21 - lvl))
+        assert np.all(cell == cell[:, :1]), (g, lvl)     # the group fits one cell of that level
 
 
 # ---------------------------------------------------------------- forces
@@ -239,11 +289,12 @@ def _single_cell_case(orc, D, quad, direction):
                       np.array([-1, -1], np.int64), np.zeros(2, np.int32))
     M, R, Q = orc.moments(tree, perm, x, m, np.zeros(3), 0)
     # group 0 = the clump (PP with itself), group 1 = the target (PC with cell 0)
+    gf = np.array([0, 40, 41], np.int64)
     pc_off = np.array([0, 0, 1], np.int64); pc = np.array([0], np.int64)
     pp_off = np.array([0, 1, 1], np.int64); pp = np.array([0], np.int64)
     a = np.zeros((3, n)); phi = np.zeros(n)
     P = orc._p
-    orc.lib().orc_tree_forces(n, P(x, orc._D), P(m, orc._D), P(perm, orc._I64), 40, 2,
+    orc.lib().orc_tree_forces(n, P(x, orc._D), P(m, orc._D), P(perm, orc._I64), 2, P(gf, orc._I64), 2,
                               P(M, orc._D), P(R, orc._D), P(Q, orc._D), P(first, orc._I64),
                               P(count, orc._I64), P(pc_off, orc._I64), P(pc, orc._I64),
                               P(pp_off, orc._I64), P(pp, orc._I64), 1.0, 0.0,
