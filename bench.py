@@ -43,10 +43,10 @@ FLOPS_PP, FLOPS_PC_QUAD, FLOPS_PC_MONO = 20, 54, 20
 # FP32 peak derived from unit counts and clocks: 152 SMs x 128 FP32 lanes x
 # 2 flops (FMA) x 2.070 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# DRAM bytes per walk launch from ncu (dram__bytes_read.sum + write.sum) on a
-# smaller case of the same kernel, per particle; None when the kernel has
-# changed since the counters were taken.
-WALK_DRAM_BYTES_PER_PARTICLE = None
+# DRAM bytes per walk launch from ncu (dram__bytes_read.sum + write.sum) on the
+# N = 1e7 galaxy case of the same kernel, per particle (scaled by N below);
+# None when the kernel has changed since the counters were taken.
+WALK_DRAM_BYTES_PER_PARTICLE = 1037
 
 
 def _args():

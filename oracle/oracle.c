@@ -12,8 +12,8 @@
  *   orc_box           root box: lo = min, L = smallest power of two > extent.
  *   orc_keys          21-bit quantisation per axis, 63-bit Morton interleave.
  *   orc_sort          order by (key, original index).
- *   orc_octree        octree of Sec. 2 ("eight octants until no more than
- *                     one particle per subdomain"), generalised to a leaf
+ *   orc_octree        octree of Sec. 2 (space split into octants, recursively,
+ *                     down to single-particle cells), generalised to a leaf
  *                     capacity, numbered breadth first.
  *   orc_moments       mass, centre of mass and traceless quadrupole per cell
  *                     (Sec. 2: far groups act through their total mass at the

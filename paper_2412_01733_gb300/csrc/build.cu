@@ -17,30 +17,35 @@ namespace treegb {
 template <typename Real>
 __global__ void __launch_bounds__(256) k_box_partial(const Real *__restrict__ x, int64_t n,
                                                      double *__restrict__ part, int32_t *dstatus) {
+    // min/max are exact in the input precision; widen to FP64 once per warp
     __shared__ double sh[6][8];
-    double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    const Real big = sizeof(Real) == 4 ? (Real)FLT_MAX : (Real)DBL_MAX;
+    Real mn[3] = {big, big, big}, mx[3] = {-big, -big, -big};
     bool bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            double v = (double)x[d * n + i];
+            const Real v = x[d * n + i];
             if (!isfinite(v)) { bad = true; continue; }
-            mn[d] = fmin(mn[d], v);
-            mx[d] = fmax(mx[d], v);
+            mn[d] = min(mn[d], v);
+            mx[d] = max(mx[d], v);
         }
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_status(dstatus, TREE_DEV_NONFINITE);
+    double dmn[3], dmx[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
+        dmn[d] = mn[d] == big ? DBL_MAX : (double)mn[d];
+        dmx[d] = mx[d] == -big ? -DBL_MAX : (double)mx[d];
         for (int o = 16; o > 0; o >>= 1) {
-            mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
-            mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+            dmn[d] = fmin(dmn[d], __shfl_xor_sync(0xffffffffu, dmn[d], o));
+            dmx[d] = fmax(dmx[d], __shfl_xor_sync(0xffffffffu, dmx[d], o));
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
-        for (int d = 0; d < 3; ++d) { sh[d][warp] = mn[d]; sh[3 + d][warp] = mx[d]; }
+        for (int d = 0; d < 3; ++d) { sh[d][warp] = dmn[d]; sh[3 + d][warp] = dmx[d]; }
     }
     __syncthreads();
     if (threadIdx.x < 6) {

@@ -6,7 +6,7 @@
 
 #include <vector>
 
-#include "../../include/treegb.h"
+#include "treegb.h"
 
 namespace treegb {
 

@@ -19,7 +19,8 @@ __global__ void __launch_bounds__(256) k_kick_drift_box(Real *__restrict__ x, Re
                                                         int64_t n, double *__restrict__ part,
                                                         int32_t *dstatus) {
     __shared__ double sh[6][8];
-    double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    const Real big = sizeof(Real) == 4 ? (Real)FLT_MAX : (Real)DBL_MAX;
+    Real mn[3] = {big, big, big}, mx[3] = {-big, -big, -big};
     bool bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -29,23 +30,25 @@ __global__ void __launch_bounds__(256) k_kick_drift_box(Real *__restrict__ x, Re
             const Real xx = fma(tau, vv, x[d * n + i]);
             v[d * n + i] = vv;
             x[d * n + i] = xx;
-            const double w = (double)xx;
-            if (!isfinite(w)) { bad = true; continue; }
-            mn[d] = fmin(mn[d], w);
-            mx[d] = fmax(mx[d], w);
+            if (!isfinite(xx)) { bad = true; continue; }
+            mn[d] = min(mn[d], xx);
+            mx[d] = max(mx[d], xx);
         }
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_status(dstatus, TREE_DEV_NONFINITE);
+    double dmn[3], dmx[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
+        dmn[d] = mn[d] == big ? DBL_MAX : (double)mn[d];
+        dmx[d] = mx[d] == -big ? -DBL_MAX : (double)mx[d];
         for (int o = 16; o > 0; o >>= 1) {
-            mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
-            mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+            dmn[d] = fmin(dmn[d], __shfl_xor_sync(0xffffffffu, dmn[d], o));
+            dmx[d] = fmax(dmx[d], __shfl_xor_sync(0xffffffffu, dmx[d], o));
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
-        for (int d = 0; d < 3; ++d) { sh[d][warp] = mn[d]; sh[3 + d][warp] = mx[d]; }
+        for (int d = 0; d < 3; ++d) { sh[d][warp] = dmn[d]; sh[3 + d][warp] = dmx[d]; }
     }
     __syncthreads();
     if (threadIdx.x < 6) {
@@ -55,7 +58,6 @@ __global__ void __launch_bounds__(256) k_kick_drift_box(Real *__restrict__ x, Re
         part[blockIdx.x * 8 + c] = r;
     }
 }
-
 
 cudaError_t launch_kick_drift_box(TreeWorkspace *ws, void *x, void *v, const void *a, double tau,
                                   int64_t n, cudaStream_t s) {
@@ -73,24 +75,37 @@ cudaError_t launch_kick_drift_box(TreeWorkspace *ws, void *x, void *v, const voi
 // ============================================================== diagnostics (FP64)
 // E_kin = 1/2 sum m v^2, W = 1/2 sum m phi, P = sum m v, L = sum m x cross v.
 // Fixed grid and fixed reduction order: deterministic.
+// Per-particle products in the input precision, summed in that precision
+// over runs of 32 particles per thread, then accumulated in FP64.
 template <typename Real>
 __global__ void __launch_bounds__(256) k_diag_partial(const Real *__restrict__ x, const Real *__restrict__ v,
                                                       const Real *__restrict__ m, const Real *__restrict__ phi,
                                                       int64_t n, double *__restrict__ part) {
     __shared__ double sh[8][8];
     double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    Real r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int run = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double mi = (double)m[i];
-        const double x0 = x[i], x1 = x[n + i], x2 = x[2 * n + i];
-        const double v0 = v[i], v1 = v[n + i], v2 = v[2 * n + i];
-        q[0] += 0.5 * mi * (v0 * v0 + v1 * v1 + v2 * v2);
-        if (phi) q[1] += 0.5 * mi * (double)phi[i];
-        q[2] += mi * v0; q[3] += mi * v1; q[4] += mi * v2;
-        q[5] += mi * (x1 * v2 - x2 * v1);
-        q[6] += mi * (x2 * v0 - x0 * v2);
-        q[7] += mi * (x0 * v1 - x1 * v0);
+        const Real mi = m[i];
+        const Real x0 = x[i], x1 = x[n + i], x2 = x[2 * n + i];
+        const Real v0 = v[i], v1 = v[n + i], v2 = v[2 * n + i];
+        r[0] += mi * (v0 * v0 + v1 * v1 + v2 * v2);
+        if (phi) r[1] += mi * phi[i];
+        r[2] += mi * v0; r[3] += mi * v1; r[4] += mi * v2;
+        r[5] += mi * (x1 * v2 - x2 * v1);
+        r[6] += mi * (x2 * v0 - x0 * v2);
+        r[7] += mi * (x0 * v1 - x1 * v0);
+        if (++run == 32) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) { q[c] += (double)r[c]; r[c] = 0; }
+            run = 0;
+        }
     }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) q[c] += (double)r[c];
+    q[0] *= 0.5;
+    q[1] *= 0.5;
 #pragma unroll
     for (int c = 0; c < 8; ++c)
         for (int o = 16; o > 0; o >>= 1) q[c] += __shfl_xor_sync(0xffffffffu, q[c], o);
@@ -99,9 +114,9 @@ __global__ void __launch_bounds__(256) k_diag_partial(const Real *__restrict__ x
         for (int c = 0; c < 8; ++c) sh[c][warp] = q[c];
     __syncthreads();
     if (threadIdx.x < 8) {
-        double r = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[threadIdx.x][w];
-        part[blockIdx.x * 8 + threadIdx.x] = r;
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[threadIdx.x][w];
+        part[blockIdx.x * 8 + threadIdx.x] = t;
     }
 }
 
@@ -276,9 +291,17 @@ __global__ void k_group_scan(uint32_t *bucket) {
 __global__ void __launch_bounds__(256) k_group_scatter(const uint32_t *__restrict__ gkey, const uint32_t *__restrict__ ctr,
                                                        uint32_t *bucket, uint32_t *__restrict__ order) {
     const uint32_t ng = ctr[kCtrGroups];
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
-        const uint32_t k = gkey[g];
-        order[atomicAdd(bucket + 32 + k, 1u)] = (uint32_t)g;
+    const int lane = threadIdx.x & 31;
+    // warp-uniform trip count, one atomic per distinct key in a warp
+    for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; b < ng; b += gridDim.x * blockDim.x) {
+        const uint32_t g = b + lane;
+        const uint32_t k = g < ng ? gkey[g] : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, k);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (g < ng && lane == leader) base = atomicAdd(bucket + 32 + k, (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (g < ng) order[base + __popc(peers & lanemask_lt())] = g;
     }
 }
 
