@@ -60,6 +60,11 @@ def _args():
                     help="particles of the oracle's bounded sample (same galaxy recipe)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the main leg only (no FP64 leg, error check, e2e, CPU baseline)")
+    ap.add_argument("--study", choices=["theta", "threads"], default=None,
+                    help="theta: precision study on the Plummer N=2^20 config (force error vs direct sum, "
+                         "energy drift, FP32 vs FP64 time per force, theta in {0.4,0.5,0.7,1.0}); "
+                         "threads: T(M), speedup and efficiency of the CPU oracle vs host threads M")
+    ap.add_argument("--study-steps", type=int, default=100)
     return ap.parse_args()
 
 
@@ -343,8 +348,98 @@ def run_reference(a):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------- studies
+def study_theta(a):
+    """Plummer N = 1,048,576, eps = 0.005, quadrupole cells, theta in {0.4, 0.5, 0.7, 1.0}: force error of
+    the FP32 and FP64 tree against the FP64 direct sum on 4096 sampled particles, FP32 / FP64 time per
+    force evaluation, and the relative energy drift over K KDK steps (tau = 0.005)."""
+    import torch
+
+    from paper_2412_01733_gb300 import build, inputs, treegb
+    build.build()
+    n, eps, tau = 1 << 20, 0.005, 0.005
+    x, v, m = inputs.plummer(n, SEED, device="cuda", dtype=torch.float64)
+    g = torch.Generator().manual_seed(SEED)
+    tgt = torch.randint(0, n, (4096,), generator=g).cuda()
+    ref_ws = treegb.Workspace(n, precision="f64", eps=eps)
+    a_ref, p_ref = ref_ws.direct(x.contiguous(), m.contiguous(), tgt, precision="f64")
+    del ref_ws
+
+    def timed(fn):
+        fn()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(); out = fn(); e1.record(); torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    for theta in (0.4, 0.5, 0.7, 1.0):
+        row = {"study": "theta", "n": n, "eps": eps, "theta": theta, "order": "quadrupole", "leaf_cap": 16}
+        for prec, dt in (("f32", torch.float32), ("f64", torch.float64)):
+            xs, vs, ms = x.to(dt).contiguous(), v.to(dt).contiguous(), m.to(dt).contiguous()
+            ws = treegb.Workspace(n, precision=prec, eps=eps, theta=theta)
+            (acc, phi), ms_force = timed(lambda: ws.accel(xs, ms))
+            e = ((acc[:, tgt].double() - a_ref).norm(dim=0) / a_ref.norm(dim=0)).cpu()
+            inf = ws.info()
+            row[prec] = {"force_ms": ms_force, "particles_per_s": n / (ms_force / 1e3),
+                         "err_median": float(e.median()), "err_p99": float(e.quantile(0.99)),
+                         "err_max": float(e.max()), "interactions_per_particle": (inf["pp_pairs"] + inf["pc_pairs"]) / n}
+            steps = a.study_steps if prec == "f32" else max(1, a.study_steps // 10)
+            d = ws.diagnostics(xs, vs, ms, phi).cpu().numpy()
+            e0_ = d[0] + d[1]
+            for _ in range(steps):
+                ws.leapfrog_step(xs, vs, ms, acc, tau, phi=phi)
+            d = ws.diagnostics(xs, vs, ms, phi).cpu().numpy()
+            row[prec]["energy_drift"] = float(abs(d[0] + d[1] - e0_) / abs(e0_))
+            row[prec]["drift_steps"] = steps
+            if ws.status() != 0:
+                row[prec]["status"] = ws.status()
+            del ws, xs, vs, ms, acc, phi
+            torch.cuda.empty_cache()
+        row["fp32_speedup_vs_fp64"] = row["f64"]["force_ms"] / row["f32"]["force_ms"]
+        print(json.dumps(row), flush=True)
+
+
+def study_threads(a):
+    """The paper's own measurement (Sec. 3, Eqs. 6-7) on the FP64 CPU oracle: mean time T(M) of one tree
+    force evaluation over 10 repetitions with its standard error, speedup S = T(1)/T(M) and efficiency
+    E = S/M, for M host threads, galaxy recipe at N = 1e5 and 1e6, theta = 1."""
+    import os as _os
+
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2412_01733_gb300 import inputs
+    ncpu = _os.cpu_count() or 1
+    ms_list = sorted({1, 2, 4, 8, ncpu // 2, ncpu} - {0})
+    for n in (100_000, 1_000_000):
+        x, _, m = inputs.galaxy(n, SEED, dtype=torch.float64)
+        x, m = x.numpy(), m.numpy()
+        res = {}
+        for M in ms_list:
+            O.set_threads(M)
+            reps = 10 if n <= 100_000 else 5
+            ts = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                O.tree_forces(x, m, eps=PARAMS["eps"], theta=1.0, lcap=PARAMS["leaf_cap"], gs=PARAMS["group_size"])
+                ts.append(time.perf_counter() - t0)
+            ts = np.array(ts)
+            res[M] = (ts.mean(), ts.std(ddof=1) / np.sqrt(len(ts)))
+        T1, dT1 = res[1]
+        for M, (T, dT) in res.items():
+            S = T1 / T
+            dS = (T1 * dT + T * dT1) / (T * T)
+            print(json.dumps({"study": "threads", "n": n, "threads": M, "host_cpus": ncpu, "T_s": T, "T_sem": dT,
+                              "S": S, "S_err": dS, "E": S / M, "E_err": dS / M}), flush=True)
+        O.set_threads(ncpu)
+
+
 def main():
     a = _args()
+    if a.study == "theta":
+        return study_theta(a)
+    if a.study == "threads":
+        return study_threads(a)
     if a.impl == "reference":
         run_reference(a)
     else:

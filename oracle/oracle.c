@@ -440,3 +440,144 @@ void orc_set_threads(int t) { if (t > 0) omp_set_num_threads(t); }
 int orc_threads(void) { return 1; }
 void orc_set_threads(int t) { (void)t; }
 #endif
+
+/* ------------------------------------------------------------------------ */
+/* Vector-Jacobian product of orc_tree_forces with the tree structure (order,
+ * cells, groups, lists) held fixed and the moments recomputed from (x, m).
+ * Given cotangents abar (3, n) of the accelerations and phibar (n) of the
+ * potentials (caller order), adds to xbar (3, n) and mbar (n):
+ *   PP pair (source j, target i, d = r_j - r_i, s^2 = |d|^2 + eps^2):
+ *     g = G m_j (abar_i s^-3 - 3 d (d . abar_i) s^-5) + G m_j phibar_i d s^-3
+ *     xbar_j += g, xbar_i -= g,
+ *     mbar_j += G (d . abar_i) s^-3 - G phibar_i s^-1.
+ *   PC pair (cell C, y = r_i - R): differentiate the cell expansion with
+ *     respect to y (xbar_i += ybar, Rbar_C -= ybar), M (Mbar_C) and the six
+ *     stored quadrupole components (Qbar_C).
+ *   Cell cotangents reach the members j of C (y_j = r_j - R) through the
+ *   definitions M = sum m_j, R = sum m_j r_j / M, Q = sum m_j (3 y_j y_j^T -
+ *   |y_j|^2 I), with Qf the symmetric matrix of Qbar (off-diagonal entries
+ *   halved) and f(y) = 3 y.Qf.y - |y|^2 tr(Qf):
+ *     mbar_j += Mbar + y_j . Rbar / M + f(y_j)
+ *     xbar_j += (m_j / M) Rbar + m_j (6 Qf y_j - 2 tr(Qf) y_j)
+ *   (the dependence of Q on R drops out because sum m_j y_j = 0).
+ *   Massless cells pass only Mbar on.  Serial (exact and simple). */
+void orc_tree_forces_vjp(int64_t n, const double *x, const double *m, const int64_t *perm,
+                         int64_t ng, const int64_t *gfirst, int64_t nn, const double *M, const double *R,
+                         const double *Q, const int64_t *first, const int64_t *count,
+                         const int64_t *pc_off, const int64_t *pc_list,
+                         const int64_t *pp_off, const int64_t *pp_list,
+                         double G, double eps, int32_t quad, const double *abar, const double *phibar,
+                         double *xbar, double *mbar)
+{
+    const double eps2 = eps * eps;
+    double *cb = (double *)calloc((size_t)(nn > 0 ? nn : 1) * 10, sizeof(double));  /* Mbar, Rbar[3], Qbar[6] */
+    for (int64_t g = 0; g < ng; ++g) {
+        for (int64_t s = gfirst[g]; s < gfirst[g + 1]; ++s) {
+            const int64_t i = perm[s];
+            const double xi = x[i], yi = x[n + i], zi = x[2 * n + i];
+            const double bx = abar[i], by = abar[n + i], bz = abar[2 * n + i];
+            const double pb = phibar ? phibar[i] : 0.0;
+            for (int64_t e = pc_off[g]; e < pc_off[g + 1]; ++e) {
+                const int64_t c = pc_list[e];
+                const double yx = xi - R[c], yy = yi - R[nn + c], yz = zi - R[2 * nn + c];
+                const double r2 = yx * yx + yy * yy + yz * yz + eps2;
+                const double r = sqrt(r2);
+                const double i1 = 1.0 / r, i2 = 1.0 / r2;
+                const double i3 = i1 * i2, i5 = i3 * i2, i7 = i5 * i2, i9 = i7 * i2;
+                const double Mc = M[c];
+                const double yb = yx * bx + yy * by + yz * bz;
+                /* monopole: a = -G M y i3, phi = -G M i1 */
+                double gx = -G * Mc * (bx * i3 - 3.0 * yx * yb * i5) + G * Mc * pb * yx * i3;
+                double gy = -G * Mc * (by * i3 - 3.0 * yy * yb * i5) + G * Mc * pb * yy * i3;
+                double gz = -G * Mc * (bz * i3 - 3.0 * yz * yb * i5) + G * Mc * pb * yz * i3;
+                double mb = -G * yb * i3 - G * pb * i1;
+                double qb[6] = {0, 0, 0, 0, 0, 0};
+                if (quad) {
+                    const double qxx = Q[c], qyy = Q[nn + c], qzz = Q[2 * nn + c];
+                    const double qxy = Q[3 * nn + c], qxz = Q[4 * nn + c], qyz = Q[5 * nn + c];
+                    const double Qx = qxx * yx + qxy * yy + qxz * yz;
+                    const double Qy = qxy * yx + qyy * yy + qyz * yz;
+                    const double Qz = qxz * yx + qyz * yy + qzz * yz;
+                    const double yQy = yx * Qx + yy * Qy + yz * Qz;
+                    const double Qb = Qx * bx + Qy * by + Qz * bz;      /* (Q y) . abar */
+                    /* a_q = G Q y i5 - 2.5 G yQy y i7 ;  phi_q = -0.5 G yQy i5
+                     * d/dy of abar.a_q = G [Q abar i5 - 5 (Qy.abar) y i7 - 2.5 (2 Qy (y.abar) + yQy abar) i7
+                     *                       + 17.5 yQy (y.abar) y i9]
+                     * d/dy of pb phi_q = pb G [-Qy i5 + 2.5 yQy y i7] */
+                    const double Qbx = qxx * bx + qxy * by + qxz * bz;
+                    const double Qby = qxy * bx + qyy * by + qyz * bz;
+                    const double Qbz = qxz * bx + qyz * by + qzz * bz;
+                    gx += G * (Qbx * i5 - 5.0 * Qb * yx * i7 - 2.5 * (2.0 * Qx * yb + yQy * bx) * i7 + 17.5 * yQy * yb * yx * i9)
+                        + pb * G * (-Qx * i5 + 2.5 * yQy * yx * i7);
+                    gy += G * (Qby * i5 - 5.0 * Qb * yy * i7 - 2.5 * (2.0 * Qy * yb + yQy * by) * i7 + 17.5 * yQy * yb * yy * i9)
+                        + pb * G * (-Qy * i5 + 2.5 * yQy * yy * i7);
+                    gz += G * (Qbz * i5 - 5.0 * Qb * yz * i7 - 2.5 * (2.0 * Qz * yb + yQy * bz) * i7 + 17.5 * yQy * yb * yz * i9)
+                        + pb * G * (-Qz * i5 + 2.5 * yQy * yz * i7);
+                    /* d/dQ (stored components): abar.a_q = G i5 (y^T Qf abar) - 2.5 G i7 yb (y^T Qf y)
+                     * and pb phi_q = -0.5 G pb i5 (y^T Qf y); a diagonal entry appears once,
+                     * an off-diagonal stored entry twice (Q[a][b] and Q[b][a]). */
+                    const double ca = G * i5, cb2 = -2.5 * G * i7 * yb - 0.5 * G * pb * i5;
+                    qb[0] = ca * yx * bx + cb2 * yx * yx;
+                    qb[1] = ca * yy * by + cb2 * yy * yy;
+                    qb[2] = ca * yz * bz + cb2 * yz * yz;
+                    qb[3] = ca * (yx * by + yy * bx) + cb2 * 2.0 * yx * yy;
+                    qb[4] = ca * (yx * bz + yz * bx) + cb2 * 2.0 * yx * yz;
+                    qb[5] = ca * (yy * bz + yz * by) + cb2 * 2.0 * yy * yz;
+                }
+                xbar[i] += gx; xbar[n + i] += gy; xbar[2 * n + i] += gz;
+                double *cc = cb + 10 * c;
+                cc[0] += mb;
+                cc[1] -= gx; cc[2] -= gy; cc[3] -= gz;
+                for (int k = 0; k < 6; ++k) cc[4 + k] += qb[k];
+            }
+            for (int64_t e = pp_off[g]; e < pp_off[g + 1]; ++e) {
+                const int64_t c = pp_list[e];
+                for (int64_t t = first[c]; t < first[c] + count[c]; ++t) {
+                    const int64_t j = perm[t];
+                    if (j == i) continue;
+                    const double dx = x[j] - xi, dy = x[n + j] - yi, dz = x[2 * n + j] - zi;
+                    const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+                    const double r = sqrt(r2);
+                    const double i1 = 1.0 / r, i3 = i1 / r2, i5 = i3 / r2;
+                    const double db = dx * bx + dy * by + dz * bz;
+                    const double gm = G * m[j];
+                    const double gx = gm * (bx * i3 - 3.0 * dx * db * i5) + gm * pb * dx * i3;
+                    const double gy = gm * (by * i3 - 3.0 * dy * db * i5) + gm * pb * dy * i3;
+                    const double gz = gm * (bz * i3 - 3.0 * dz * db * i5) + gm * pb * dz * i3;
+                    xbar[j] += gx; xbar[n + j] += gy; xbar[2 * n + j] += gz;
+                    xbar[i] -= gx; xbar[n + i] -= gy; xbar[2 * n + i] -= gz;
+                    mbar[j] += G * db * i3 - G * pb * i1;
+                }
+            }
+        }
+    }
+    /* push every cell's cotangent to its members, from the definitions */
+    for (int64_t c = 0; c < nn; ++c) {
+        const double *cc = cb + 10 * c;
+        int nz = 0;
+        for (int k = 0; k < 10; ++k) nz |= cc[k] != 0.0;
+        if (!nz) continue;
+        const double Mc = M[c];
+        for (int64_t t = first[c]; t < first[c] + count[c]; ++t) {
+            const int64_t j = perm[t];
+            mbar[j] += cc[0];
+            if (Mc == 0.0) continue;
+            const double yx = x[j] - R[c], yy = x[n + j] - R[nn + c], yz = x[2 * n + j] - R[2 * nn + c];
+            /* symmetric cotangent matrix: diagonal as stored, off-diagonal halved */
+            const double fxx = cc[4], fyy = cc[5], fzz = cc[6];
+            const double fxy = 0.5 * cc[7], fxz = 0.5 * cc[8], fyz = 0.5 * cc[9];
+            const double tr = fxx + fyy + fzz;
+            const double Fx = fxx * yx + fxy * yy + fxz * yz;
+            const double Fy = fxy * yx + fyy * yy + fyz * yz;
+            const double Fz = fxz * yx + fyz * yy + fzz * yz;
+            const double y2 = yx * yx + yy * yy + yz * yz;
+            const double f = 3.0 * (yx * Fx + yy * Fy + yz * Fz) - y2 * tr;
+            mbar[j] += (yx * cc[1] + yy * cc[2] + yz * cc[3]) / Mc + f;
+            const double w = m[j] / Mc;
+            xbar[j] += w * cc[1] + m[j] * (6.0 * Fx - 2.0 * tr * yx);
+            xbar[n + j] += w * cc[2] + m[j] * (6.0 * Fy - 2.0 * tr * yy);
+            xbar[2 * n + j] += w * cc[3] + m[j] * (6.0 * Fz - 2.0 * tr * yz);
+        }
+    }
+    free(cb);
+}

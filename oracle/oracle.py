@@ -49,6 +49,8 @@ def lib():
                                 _I64, _I64, _I64, _I64]
         L.orc_tree_forces.argtypes = [i64, _D, _D, _I64, i64, _I64, i64, _D, _D, _D, _I64, _I64,
                                       _I64, _I64, _I64, _I64, dbl, dbl, i32, _D, _D]
+        L.orc_tree_forces_vjp.argtypes = [i64, _D, _D, _I64, i64, _I64, i64, _D, _D, _D, _I64, _I64,
+                                          _I64, _I64, _I64, _I64, dbl, dbl, i32, _D, _D, _D, _D]
         L.orc_threads.restype = ctypes.c_int
         L.orc_set_threads.argtypes = [ctypes.c_int]
         _lib = L
@@ -264,3 +266,87 @@ def diagnostics(x, v, m, phi):
     P = np.sum(m * v, axis=1)
     L = np.sum(m * np.cross(x.T, v.T).T, axis=1)
     return dict(ekin=ek, epot=w, etot=ek + w, P=P, L=L)
+
+
+# --------------------------------------------------------------------------- #
+# Adjoint of the tree force and of the leapfrog with the tree structure held
+# fixed per force evaluation (order, cells, groups, lists from the primal
+# state; moments recomputed from the perturbed positions and masses).
+def tree_forces_frozen(r: TreeResult, x, m, *, G=1.0, eps=0.0, quad=True):
+    """Forces of (x, m) through the structure of r: moments recomputed, lists reused."""
+    x = _f64(x); m = _f64(m)
+    n = m.shape[0]
+    M, R, Q = moments(r.tree, r.perm, x, m, r.lo, r.k)
+    a = np.zeros((3, n)); phi = np.zeros(n)
+    gf, tr = r.gfirst, r.tree
+    lib().orc_tree_forces(n, _p(x, _D), _p(m, _D), _p(r.perm, _I64), gf.shape[0] - 1, _p(gf, _I64), tr.nn,
+                          _p(M, _D), _p(R, _D), _p(Q, _D), _p(tr.first, _I64), _p(tr.count, _I64),
+                          _p(r.pc_off, _I64), _p(r.pc_list, _I64), _p(r.pp_off, _I64), _p(r.pp_list, _I64),
+                          float(G), float(eps), 1 if quad else 0, _p(a, _D), _p(phi, _D))
+    return a, phi
+
+
+def tree_forces_vjp(r: TreeResult, x, m, abar, phibar=None, *, G=1.0, eps=0.0, quad=True):
+    """(xbar, mbar) = VJP of (a, phi) = tree_forces_frozen(r, x, m) with cotangents (abar, phibar)."""
+    x = _f64(x); m = _f64(m); abar = _f64(abar)
+    phibar = None if phibar is None else _f64(phibar)
+    n = m.shape[0]
+    M, R, Q = moments(r.tree, r.perm, x, m, r.lo, r.k)
+    xbar = np.zeros((3, n)); mbar = np.zeros(n)
+    gf, tr = r.gfirst, r.tree
+    lib().orc_tree_forces_vjp(n, _p(x, _D), _p(m, _D), _p(r.perm, _I64), gf.shape[0] - 1, _p(gf, _I64), tr.nn,
+                              _p(M, _D), _p(R, _D), _p(Q, _D), _p(tr.first, _I64), _p(tr.count, _I64),
+                              _p(r.pc_off, _I64), _p(r.pc_list, _I64), _p(r.pp_off, _I64), _p(r.pp_list, _I64),
+                              float(G), float(eps), 1 if quad else 0, _p(abar, _D), _p(phibar, _D),
+                              _p(xbar, _D), _p(mbar, _D))
+    return xbar, mbar
+
+
+def kdk_forward(x, v, m, tau, nsteps, **tree_kw):
+    """Eqs. 2-5 with tree forces; returns the states x_n, v_n, a_n, phi_n (n = 0..K) and the
+    structure used at every x_n (the primal trajectory of the adjoint)."""
+    x = _f64(x).copy(); v = _f64(v).copy(); m = _f64(m)
+    r = tree_forces(x, m, **tree_kw)
+    xs, vs, as_, ps, rs = [x], [v], [r.a], [r.phi], [r]
+    for _ in range(int(nsteps)):
+        vh = vs[-1] + 0.5 * tau * as_[-1]
+        xn = xs[-1] + tau * vh
+        r = tree_forces(xn, m, **tree_kw)
+        vs.append(vh + 0.5 * tau * r.a); xs.append(xn); as_.append(r.a); ps.append(r.phi); rs.append(r)
+    return xs, vs, as_, ps, rs
+
+
+def kdk_frozen(x, v, m, tau, structures, *, G=1.0, eps=0.0, quad=True):
+    """The same K steps with every force evaluated through the given structures (for finite
+    differences of the frozen-structure map).  Returns x_K, v_K, phi_K."""
+    x = _f64(x).copy(); v = _f64(v).copy(); m = _f64(m)
+    a, phi = tree_forces_frozen(structures[0], x, m, G=G, eps=eps, quad=quad)
+    for r in structures[1:]:
+        v = v + 0.5 * tau * a
+        x = x + tau * v
+        a, phi = tree_forces_frozen(r, x, m, G=G, eps=eps, quad=quad)
+        v = v + 0.5 * tau * a
+    return x, v, phi
+
+
+def kdk_adjoint(xs, m, tau, structures, xbar_K, vbar_K, phibar_K=None, *, G=1.0, eps=0.0, quad=True):
+    """Reverse sweep of Eqs. 2-5 through frozen structures.  Given cotangents of x_K, v_K and of the
+    final potentials phi_K, returns (xbar_0, vbar_0, mbar).  Step n maps (x_n, v_n, a_n) to
+    (x_{n+1}, v_{n+1}, a_{n+1}): v' = v_n + tau/2 a_n, x_{n+1} = x_n + tau v', a_{n+1} = F(x_{n+1}),
+    v_{n+1} = v' + tau/2 a_{n+1}; a_0 = F(x_0)."""
+    m = _f64(m)
+    K = len(xs) - 1
+    h = 0.5 * tau
+    xb = _f64(xbar_K).copy(); vb = _f64(vbar_K).copy(); mb = np.zeros_like(m)
+    ab = np.zeros_like(xb)             # cotangent of a_{n+1}
+    pb = None if phibar_K is None else _f64(phibar_K)
+    for nstep in range(K - 1, -1, -1):
+        ab = ab + h * vb                                   # v_{n+1} = v' + h a_{n+1}
+        dx, dm = tree_forces_vjp(structures[nstep + 1], xs[nstep + 1], m, ab,
+                                 pb if nstep == K - 1 else None, G=G, eps=eps, quad=quad)
+        xb = xb + dx; mb = mb + dm
+        vb = vb + tau * xb                                  # x_{n+1} = x_n + tau v'
+        ab = h * vb                                         # v' = v_n + h a_n
+    dx, dm = tree_forces_vjp(structures[0], xs[0], m, ab, pb if K == 0 else None, G=G, eps=eps, quad=quad)
+    xb = xb + dx; mb = mb + dm
+    return xb, vb, mb
