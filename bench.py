@@ -374,7 +374,8 @@ def study_theta(a):
     for theta in (0.4, 0.5, 0.7, 1.0):
         row = {"study": "theta", "n": n, "eps": eps, "theta": theta, "order": "quadrupole", "leaf_cap": 16}
         for prec, dt in (("f32", torch.float32), ("f64", torch.float64)):
-            xs, vs, ms = x.to(dt).contiguous(), v.to(dt).contiguous(), m.to(dt).contiguous()
+            # explicit copies: the leapfrog below advances them in place
+            xs, vs, ms = x.to(dt).clone(), v.to(dt).clone(), m.to(dt).clone()
             ws = treegb.Workspace(n, precision=prec, eps=eps, theta=theta)
             (acc, phi), ms_force = timed(lambda: ws.accel(xs, ms))
             e = ((acc[:, tgt].double() - a_ref).norm(dim=0) / a_ref.norm(dim=0)).cpu()

@@ -130,7 +130,8 @@ typedef struct {
 #define TREE_PHASE_LISTS 7   /* interaction-list count/scan/emit */
 #define TREE_PHASE_DIAG 8    /* diagnostics reductions */
 #define TREE_PHASE_DIRECT 9  /* direct summation */
-#define TREE_NPHASES 10
+#define TREE_PHASE_ADJOINT 10 /* tree_forces_adjoint */
+#define TREE_NPHASES 11
 
 /* Fills *p with the defaults: G = 1, eps = 0.01, theta = 0.7, order = 2,
  * leaf_cap = 16, group_size = 32, stack_depth = 1024, precision = TREE_F32,
@@ -168,6 +169,36 @@ tree_status_t tree_moments(TreeWorkspace *ws, const void *x, const void *m, void
  * lists in ws (extra device memory, allocated on first use, synchronises
  * the stream once to size it). */
 tree_status_t tree_forces(TreeWorkspace *ws, void *a, void *phi, int32_t flags, void *stream);
+
+/* Vector-Jacobian product of the last tree_forces (not part of the paper:
+ * gradients through the method).  The tree structure of the last build --
+ * key order, cells, walk groups and the interaction lists, which must have
+ * been stored by tree_forces(TREE_FLAG_EMIT_LISTS) -- is held fixed; the
+ * cell moments are treated as functions of (x, m), so their cotangents are
+ * carried back to the particles.  Given a_bar [3][n] (cotangent of the
+ * accelerations) and phi_bar [n] or NULL (of the potentials), ADDS the
+ * gradient to x_bar [3][n] and m_bar [n] (either may be NULL), all in the
+ * caller's order and the workspace precision.  FP64 accumulation of the
+ * cotangents.  Scratch is allocated on the first call (about 56 B per
+ * particle + 80 B per node).  Errors: TREE_ERR_STATE without stored lists. */
+tree_status_t tree_forces_adjoint(TreeWorkspace *ws, const void *a_bar, const void *phi_bar, void *x_bar,
+                                  void *m_bar, void *stream);
+
+/* One reverse step of the leapfrog (Eqs. 2-5) through the tree stored in ws,
+ * which must have been built at x_{n+1} with lists (tree_build, tree_moments,
+ * tree_forces with TREE_FLAG_EMIT_LISTS).  The forward step is
+ *   v' = v_n + tau/2 a_n,  x_{n+1} = x_n + tau v',  a_{n+1} = F(x_{n+1}),
+ *   v_{n+1} = v' + tau/2 a_{n+1}.
+ * On entry x_bar, v_bar hold the cotangents of x_{n+1}, v_{n+1} and a_bar the
+ * cotangent of a_{n+1} from its later use (zero at the last step); phi_bar
+ * (or NULL) the cotangent of the potentials at x_{n+1}.  The call computes
+ *   a_bar += tau/2 v_bar;  (x_bar, m_bar) += VJP of F at x_{n+1};
+ *   v_bar += tau x_bar;  a_bar = tau/2 v_bar,
+ * leaving the cotangents of x_n, v_n and a_n (= F(x_n)), and accumulating the
+ * mass gradient in m_bar.  All [3][n] / [n] device arrays in the caller's order
+ * and the workspace precision.  Not part of the paper. */
+tree_status_t leapfrog_adjoint_step(TreeWorkspace *ws, void *x_bar, void *v_bar, void *a_bar, void *m_bar,
+                                    const void *phi_bar, double tau, void *stream);
 
 /* tree_build + tree_moments + tree_forces on (x, m, n). */
 tree_status_t tree_accel(TreeWorkspace *ws, const void *x, const void *m, int64_t n,

@@ -17,7 +17,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtreegb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "build.cu", "groups.cu", "moments.cu", "integrate.cu", "walk_f32.cu", "walk_f64.cu"]
+SOURCES = ["api.cu", "build.cu", "groups.cu", "moments.cu", "integrate.cu", "adjoint.cu", "walk_f32.cu",
+           "walk_f64.cu"]
 
 
 def nvcc() -> str:

@@ -71,7 +71,8 @@ void free_all(TreeWorkspace *ws) {
                     ws->ctr, ws->part, ws->box, ws->spos, ws->nfirst, ws->ncount, ws->ngeo, ws->nlink,
                     ws->mom64, ws->mom_a, ws->mom_b, ws->mom_c, ws->dstatus, ws->stats, ws->gstat,
                     ws->list_cnt, ws->pc_list, ws->pp_list, ws->direct_part, ws->dmac, ws->gorder,
-                    ws->gkey, ws->gbucket, ws->gfirst, ws->plev, ws->ccount, ws->coff, ws->gscan_status};
+                    ws->gkey, ws->gbucket, ws->gfirst, ws->plev, ws->ccount, ws->coff, ws->gscan_status,
+                    ws->adj_cot, ws->adj_xt, ws->adj_xg, ws->adj_mg, ws->adj_ccot};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : ws->ev) cudaEventDestroy(e);
@@ -369,6 +370,45 @@ tree_status_t tree_forces(TreeWorkspace *ws, void *a, void *phi, int32_t flags, 
     }
     WalkOut out{a, phi, nullptr, 0.0};
     return walk(ws, kWalkForce, out, s);
+}
+
+static tree_status_t adjoint_ready(TreeWorkspace *ws) {
+    if (!ws->has_moments || ws->list_groups < 0) return TREE_ERR_STATE;
+    if (!ws->adj_xt) {
+        const size_t N = (size_t)ws->n_max, NC = (size_t)ws->node_cap;
+        const size_t v4 = ws->p.precision == TREE_F64 ? sizeof(double4a) : sizeof(float4);
+        if (!(dalloc((unsigned char **)&ws->adj_cot, N * v4) && dalloc(&ws->adj_xt, 3 * N) &&
+              dalloc(&ws->adj_xg, 3 * N) && dalloc(&ws->adj_mg, N) && dalloc(&ws->adj_ccot, 10 * NC))) {
+            return TREE_ERR_ALLOC;
+        }
+    }
+    return TREE_OK;
+}
+
+tree_status_t tree_forces_adjoint(TreeWorkspace *ws, const void *a_bar, const void *phi_bar, void *x_bar, void *m_bar,
+                                  void *stream) {
+    if (!ws) return TREE_ERR_ARG;
+    if (ws->n > 0 && (!a_bar || (!x_bar && !m_bar))) return TREE_ERR_ARG;
+    tree_status_t st = adjoint_ready(ws);
+    if (st != TREE_OK) return st;
+    if (ws->n == 0) return TREE_OK;
+    cudaStream_t s = as_stream(stream);
+    PhaseScope ph(ws, TREE_PHASE_ADJOINT, s);
+    TRY_CUDA(launch_adjoint(ws, a_bar, phi_bar, x_bar, m_bar, s));
+    return TREE_OK;
+}
+
+tree_status_t leapfrog_adjoint_step(TreeWorkspace *ws, void *x_bar, void *v_bar, void *a_bar, void *m_bar,
+                                    const void *phi_bar, double tau, void *stream) {
+    if (!ws || !isfinite(tau)) return TREE_ERR_ARG;
+    if (ws->n > 0 && (!x_bar || !v_bar || !a_bar || !m_bar)) return TREE_ERR_ARG;
+    tree_status_t st = adjoint_ready(ws);
+    if (st != TREE_OK) return st;
+    if (ws->n == 0) return TREE_OK;
+    cudaStream_t s = as_stream(stream);
+    PhaseScope ph(ws, TREE_PHASE_ADJOINT, s);
+    TRY_CUDA(launch_adjoint_step(ws, x_bar, v_bar, a_bar, m_bar, phi_bar, tau, s));
+    return TREE_OK;
 }
 
 tree_status_t tree_accel(TreeWorkspace *ws, const void *x, const void *m, int64_t n, void *a, void *phi,

@@ -122,6 +122,9 @@ struct TreeWorkspace {
     int64_t list_pc_cap = 0, list_pp_cap = 0, list_pc = 0, list_pp = 0;
     int64_t list_groups = -1;
     int64_t list_groups_host = 0;      // group count used by the last list emission
+    // adjoint scratch (allocated on first use)
+    void *adj_cot = nullptr;           // Vec4 (abar, phibar) in key order
+    double *adj_xt = nullptr, *adj_xg = nullptr, *adj_mg = nullptr, *adj_ccot = nullptr;
     // direct-sum scratch
     double *direct_part = nullptr;
     size_t direct_part_bytes = 0;
@@ -281,6 +284,11 @@ struct WalkOut {
 };
 cudaError_t launch_walk_f32(TreeWorkspace *ws, int mode, const WalkOut &out, cudaStream_t s);
 cudaError_t launch_walk_f64(TreeWorkspace *ws, int mode, const WalkOut &out, cudaStream_t s);
+// adjoint.cu
+cudaError_t launch_adjoint(TreeWorkspace *ws, const void *abar, const void *phibar, void *xbar, void *mbar,
+                           cudaStream_t s);
+cudaError_t launch_adjoint_step(TreeWorkspace *ws, void *xbar, void *vbar, void *abar, void *mbar,
+                                const void *phibar, double tau, cudaStream_t s);
 // integrate.cu
 cudaError_t launch_kick_drift_box(TreeWorkspace *ws, void *x, void *v, const void *a, double tau,
                                   int64_t n, cudaStream_t s);

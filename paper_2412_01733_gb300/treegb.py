@@ -20,7 +20,7 @@ TREE_OK, TREE_ERR_ARG, TREE_ERR_CUDA, TREE_ERR_ALLOC, TREE_ERR_CAPACITY, TREE_ER
 DEV_NONFINITE, DEV_STACK, DEV_NODES, DEV_TIMEOUT, DEV_LIST = 0x01, 0x02, 0x04, 0x08, 0x10
 F32, F64 = 0, 1
 FLAG_EMIT_LISTS = 0x1
-PHASES = ("box", "keys", "sort", "octree", "gather", "moments", "walk", "lists", "diag", "direct")
+PHASES = ("box", "keys", "sort", "octree", "gather", "moments", "walk", "lists", "diag", "direct", "adjoint")
 
 
 class TreeParams(ctypes.Structure):
@@ -57,6 +57,8 @@ _SIGNATURES = {
     "tree_moments": [_vp, _vp, _vp, _vp],
     "tree_forces": [_vp, _vp, _vp, _i32, _vp],
     "tree_accel": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],
+    "tree_forces_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "leapfrog_adjoint_step": [_vp, _vp, _vp, _vp, _vp, _vp, _dbl, _vp],
     "leapfrog_step": [_vp, _vp, _vp, _vp, _vp, _vp, _dbl, _i64, _vp],
     "tree_diagnostics": [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp],
     "tree_direct_forces": [_vp, _vp, _vp, _i64, _i32, _vp, _i64, _vp, _vp, _vp],
@@ -214,6 +216,30 @@ class Workspace:
         _check("tree_forces", lib().tree_forces(self._h, _ptr(a), _ptr(phi),
                                                 FLAG_EMIT_LISTS if emit_lists else 0, _stream()))
         return a, phi
+
+    def forces_adjoint(self, a_bar, phi_bar=None, x_bar=None, m_bar=None):
+        """Adds the VJP of the last tree_forces (lists stored with emit_lists=True) with cotangents
+        (a_bar, phi_bar) to x_bar (3, n) and m_bar (n,); returns them (allocated as zeros if None)."""
+        n = self.n
+        self._vec(a_bar, n, "a_bar"); self._scal(phi_bar, n, "phi_bar", optional=True)
+        if x_bar is None:
+            x_bar = torch.zeros((3, n), dtype=self.dtype, device="cuda")
+        if m_bar is None:
+            m_bar = torch.zeros((n,), dtype=self.dtype, device="cuda")
+        self._vec(x_bar, n, "x_bar"); self._scal(m_bar, n, "m_bar")
+        _check("tree_forces_adjoint", lib().tree_forces_adjoint(self._h, _ptr(a_bar), _ptr(phi_bar), _ptr(x_bar),
+                                                                _ptr(m_bar), _stream()))
+        return x_bar, m_bar
+
+    def leapfrog_adjoint_step(self, x_bar, v_bar, a_bar, m_bar, tau, phi_bar=None):
+        """One reverse leapfrog step through the tree stored at x_{n+1} (see treegb.h); in place."""
+        n = self.n
+        for t, nm in ((x_bar, "x_bar"), (v_bar, "v_bar"), (a_bar, "a_bar")):
+            self._vec(t, n, nm)
+        self._scal(m_bar, n, "m_bar"); self._scal(phi_bar, n, "phi_bar", optional=True)
+        _check("leapfrog_adjoint_step", lib().leapfrog_adjoint_step(self._h, _ptr(x_bar), _ptr(v_bar), _ptr(a_bar),
+                                                                    _ptr(m_bar), _ptr(phi_bar), float(tau),
+                                                                    _stream()))
 
     def accel(self, x, m, a=None, phi=None, want_phi=True):
         """Accelerations and potentials of (x, m) by the tree (build + moments + forces)."""
