@@ -23,9 +23,9 @@
  *          children are the non-empty octants in octant order; breadth-first
  *          numbering (level by level, ascending key prefix within a level).
  *   groups chunks of Gs consecutive sorted particles, cut between neighbours
- *          i-1, i whose keys share fewer octal digits than
- *          max(leaf level(i-1), leaf level(i)) - group_split; integer box
- *          [min q, max q + 1) per axis.
+ *          i-1, i whose keys share P < max(leaf level(i-1), leaf level(i)) -
+ *          group_split octal digits, or whose level-P cell holds more than
+ *          128 Gs particles; integer box [min q, max q + 1) per axis.
  *   MAC    a node of level l (side s = 2^(21-l), box [c, c+s)) is far for a group
  *          iff s^2 < fl(theta^2 * d2), d2 = sum_d max(0, c_d - ghi_d, glo_d - c_d - s)^2
  *          (exact integers); rejected leaves are summed particle by particle.
@@ -96,7 +96,9 @@ typedef struct {
     int32_t precision;   /* TREE_F32 or TREE_F64 */
     int32_t kahan;       /* FP32: 1 = compensated per-particle accumulation */
     int32_t group_split; /* delta: cut a group between neighbours that do not share the cell
-                            delta levels above the finer of their leaves; 0 = plain chunks */
+                            delta levels above the finer of their leaves, or whose smallest
+                            common cell holds more than 128 group_size particles;
+                            0 = plain chunks */
     int64_t node_cap;    /* node array capacity; 0 = default from n_max and leaf_cap */
 } TreeParams;
 

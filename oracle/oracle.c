@@ -273,11 +273,14 @@ void orc_moments(int64_t nn, const int64_t *first, const int64_t *count,
  * further cut between consecutive particles i, i+1 that do not share the cell
  * delta levels above the finer of their two leaves, i.e. where
  *   P(i, i+1) < max(leaf_level(i), leaf_level(i+1)) - delta,
- * P = number of leading octal digits the two keys share (21 if equal).
- * delta = 0 keeps plain chunks.  gfirst (capacity n + 1) receives the first
- * sorted index of every group and n at the end; returns the group count. */
+ * P = number of leading octal digits the two keys share (21 if equal), and
+ * where the cell of level P holding both (their smallest common cell) has more
+ * than cmax particles.  delta = 0 disables the first cut, cmax = 0 the second.
+ * gfirst (capacity n + 1) receives the first sorted index of every group and n
+ * at the end; returns the group count. */
 int64_t orc_groups(int64_t n, const uint64_t *skey, int64_t nn, const int32_t *level, const int64_t *first,
-                   const int64_t *count, const int32_t *nchild, int32_t gs, int32_t delta, int64_t *gfirst)
+                   const int64_t *count, const int32_t *nchild, int32_t gs, int32_t delta, int64_t cmax,
+                   int64_t *gfirst)
 {
     int32_t *lv = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     for (int64_t c = 0; c < nn; ++c)
@@ -286,7 +289,7 @@ int64_t orc_groups(int64_t n, const uint64_t *skey, int64_t nn, const int32_t *l
     int64_t ng = 0;
     for (int64_t i = 0; i < n; ++i) {
         int start = (i % gs) == 0;
-        if (!start && delta > 0) {
+        if (!start && (delta > 0 || cmax > 0)) {
             uint64_t d = skey[i - 1] ^ skey[i];
             int common = 21;
             if (d) {
@@ -294,7 +297,22 @@ int64_t orc_groups(int64_t n, const uint64_t *skey, int64_t nn, const int32_t *l
                 common = (62 - hb) / 3;
             }
             int lmax = lv[i - 1] > lv[i] ? lv[i - 1] : lv[i];
-            if (common < lmax - delta) start = 1;
+            if (delta > 0 && common < lmax - delta) start = 1;
+            if (!start && cmax > 0) {
+                /* particles whose keys share the first `common` digits with key i */
+                const int sh = 3 * (21 - common);
+                const uint64_t pre = sh >= 64 ? 0 : skey[i] >> sh;
+                int64_t cnt = 1;
+                for (int64_t j = i - 1; j >= 0 && cnt <= cmax; --j) {
+                    if ((sh >= 64 ? 0 : skey[j] >> sh) != pre) break;
+                    ++cnt;
+                }
+                for (int64_t j = i + 1; j < n && cnt <= cmax; ++j) {
+                    if ((sh >= 64 ? 0 : skey[j] >> sh) != pre) break;
+                    ++cnt;
+                }
+                if (cnt > cmax) start = 1;
+            }
         }
         if (start) gfirst[ng++] = i;
     }

@@ -43,7 +43,7 @@ def lib():
         L.orc_octree.argtypes = [i64, _U64, i32, i64, _I32, _U32, _I64, _I64, _I64, _I32]
         L.orc_octree.restype = i64
         L.orc_moments.argtypes = [i64, _I64, _I64, _D, _I64, i64, _D, _D, _D, _D, _D]
-        L.orc_groups.argtypes = [i64, _U64, i64, _I32, _I64, _I64, _I32, i32, i32, _I64]
+        L.orc_groups.argtypes = [i64, _U64, i64, _I32, _I64, _I64, _I32, i32, i32, i64, _I64]
         L.orc_groups.restype = i64
         L.orc_lists.argtypes = [i64, _U32, i64, _I64, dbl, i64, _I32, _U32, _I64, _I32,
                                 _I64, _I64, _I64, _I64]
@@ -168,13 +168,16 @@ def moments(tree: Octree, perm, x, m, lo, k):
     return M, R, Q
 
 
-def groups(skey, tree: Octree, gs, delta=3):
-    """First sorted index of every walk group, plus n at the end (orc_groups)."""
+def groups(skey, tree: Octree, gs, delta=3, cmax=None):
+    """First sorted index of every walk group, plus n at the end (orc_groups).
+    cmax defaults to 128 gs when delta > 0 and to 0 (no cell-size cut) for plain chunks."""
     skey = np.ascontiguousarray(skey, dtype=np.uint64)
     n = skey.shape[0]
+    if cmax is None:
+        cmax = 128 * int(gs) if delta > 0 else 0
     gf = np.zeros(n + 1, np.int64)
     ng = lib().orc_groups(n, _p(skey, _U64), tree.nn, _p(tree.level, _I32), _p(tree.first, _I64),
-                          _p(tree.count, _I64), _p(tree.nchild, _I32), int(gs), int(delta), _p(gf, _I64))
+                          _p(tree.count, _I64), _p(tree.nchild, _I32), int(gs), int(delta), cmax, _p(gf, _I64))
     return gf[: ng + 1].copy()
 
 
@@ -213,7 +216,7 @@ class TreeResult:
     phi: np.ndarray       # (n,)
 
 
-def tree_forces(x, m, *, G=1.0, eps=0.0, theta=0.7, lcap=16, gs=32, quad=True, delta=3,
+def tree_forces(x, m, *, G=1.0, eps=0.0, theta=0.7, lcap=16, gs=32, quad=True, delta=3, cmax=None,
                 want_forces=True):
     """Whole canonical tree pipeline; returns every intermediate and a, phi."""
     x = _f64(x); m = _f64(m)
@@ -224,7 +227,7 @@ def tree_forces(x, m, *, G=1.0, eps=0.0, theta=0.7, lcap=16, gs=32, quad=True, d
     tr = octree(key[perm], lcap)
     M, R, Q = moments(tr, perm, x, m, lo, k)
     qs = np.ascontiguousarray(q[:, perm])
-    gf = groups(key[perm], tr, gs, delta)
+    gf = groups(key[perm], tr, gs, delta, cmax)
     pc_off, pc, pp_off, pp = lists(qs, gf, theta, tr)
     a = np.zeros((3, n)); phi = np.zeros(n)
     if want_forces:

@@ -72,7 +72,7 @@ void free_all(TreeWorkspace *ws) {
                     ws->mom64, ws->mom_a, ws->mom_b, ws->mom_c, ws->dstatus, ws->stats, ws->gstat,
                     ws->list_cnt, ws->pc_list, ws->pp_list, ws->direct_part, ws->dmac, ws->gorder,
                     ws->gkey, ws->gbucket, ws->gfirst, ws->plev, ws->ccount, ws->coff, ws->gscan_status,
-                    ws->adj_cot, ws->adj_xt, ws->adj_xg, ws->adj_mg, ws->adj_ccot};
+                    ws->adj_cot, ws->adj_xt, ws->adj_xg, ws->adj_mg, ws->adj_ccot, ws->pleaf, ws->nparent};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : ws->ev) cudaEventDestroy(e);
@@ -199,7 +199,8 @@ tree_status_t tree_workspace_create(int64_t n_max, const TreeParams *p, TreeWork
               dalloc(&ws->stats, kStatCount) && dalloc(&ws->gstat, (size_t)ws->groups_max) &&
               dalloc(&ws->gorder, (size_t)ws->groups_max) && dalloc(&ws->gkey, (size_t)ws->groups_max) &&
               dalloc(&ws->gbucket, 64) && dalloc(&ws->gfirst, (size_t)ws->groups_max + 1) &&
-              dalloc(&ws->plev, N) && dalloc(&ws->ccount, (size_t)chunks_max) && dalloc(&ws->coff, (size_t)chunks_max) &&
+              dalloc(&ws->plev, N) && dalloc(&ws->pleaf, N) && dalloc(&ws->nparent, NC) &&
+              dalloc(&ws->ccount, (size_t)chunks_max) && dalloc(&ws->coff, (size_t)chunks_max) &&
               dalloc(&ws->gscan_status, (size_t)(chunks_max / 2048 + 2)) &&
               dalloc(&ws->dmac, kLevels);
     if (!ok) {

@@ -322,7 +322,7 @@ cudaError_t launch_sort(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
 }
 
 // ============================================================== octree
-__global__ void k_tree_init(uint32_t *ctr, uint32_t *nfirst, uint32_t *ncount, int64_t n) {
+__global__ void k_tree_init(uint32_t *ctr, uint32_t *nfirst, uint32_t *ncount, uint32_t *nparent, int64_t n) {
     const int t = threadIdx.x;
     if (t < kLevels + 1) {
         ctr[kCtrLevelTrunc + t] = 0xffffffffu;
@@ -335,6 +335,7 @@ __global__ void k_tree_init(uint32_t *ctr, uint32_t *nfirst, uint32_t *ncount, i
         ctr[kCtrLevelRawEnd + 0] = n > 0 ? 1u : 0u;
         nfirst[0] = 0;
         ncount[0] = (uint32_t)n;
+        nparent[0] = 0;
     }
 }
 
@@ -356,8 +357,8 @@ __device__ __forceinline__ uint32_t digit_lower_bound(const uint64_t *__restrict
 // children's ranges are written for level L+1.
 __global__ void __launch_bounds__(kLevelThreads) k_level(
     int L, const uint64_t *__restrict__ skey, uint32_t *__restrict__ nfirst, uint32_t *__restrict__ ncount,
-    uint4 *__restrict__ ngeo, uint2 *__restrict__ nlink, uint32_t *ctr, uint32_t *lstatus,
-    uint32_t lcap, uint32_t node_cap, int32_t *dstatus) {
+    uint4 *__restrict__ ngeo, uint2 *__restrict__ nlink, uint32_t *__restrict__ nparent, uint32_t *ctr,
+    uint32_t *lstatus, uint32_t lcap, uint32_t node_cap, int32_t *dstatus) {
     __shared__ uint32_t s_tile, s_excl, s_total;
     __shared__ uint32_t wt[32];
     const uint32_t start = ctr[kCtrLevelStart + L];
@@ -425,6 +426,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(
                 if (b[o + 1] > b[o]) {
                     nfirst[c] = b[o];
                     ncount[c] = b[o + 1] - b[o];
+                    nparent[c] = node;
                     ++c;
                 }
             }
@@ -435,14 +437,14 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(
 }
 
 cudaError_t launch_octree(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
-    k_tree_init<<<1, 32, 0, s>>>(ws->ctr, ws->nfirst, ws->ncount, n);
+    k_tree_init<<<1, 32, 0, s>>>(ws->ctr, ws->nfirst, ws->ncount, ws->nparent, n);
     double maxl = 1.0;
     for (int L = 0; L < kLevels; ++L) {
         double bound = fmin(fmin(maxl, (double)n), (double)ws->node_cap);
         int nb = grid_for((int64_t)bound, kLevelThreads, 152 * 8);
         uint32_t *lst = ws->level_status + (size_t)L * ws->level_tiles_max;
         k_level<<<nb, kLevelThreads, 0, s>>>(L, ws->key, ws->nfirst, ws->ncount, ws->ngeo, ws->nlink,
-                                             ws->ctr, lst, (uint32_t)ws->p.leaf_cap,
+                                             ws->nparent, ws->ctr, lst, (uint32_t)ws->p.leaf_cap,
                                              (uint32_t)ws->node_cap, ws->dstatus);
         maxl *= 8.0;
     }

@@ -108,6 +108,8 @@ struct TreeWorkspace {
     uint4 *gstat = nullptr;            // per walk group: {n_pc, n_pp particles, max stack, n_pp leaves}
     uint32_t *gfirst = nullptr;        // walk groups: first sorted index of each, then n
     uint8_t *plev = nullptr;           // leaf level of every sorted particle
+    uint32_t *pleaf = nullptr;         // leaf node of every sorted particle
+    uint32_t *nparent = nullptr;       // parent of every node (root: itself)
     uint32_t *ccount = nullptr, *coff = nullptr;  // groups starting in each Gs chunk / their offsets
     uint32_t *gscan_status = nullptr;  // look-back words of the chunk scan
     int64_t walk_grid = 0;             // resident walk blocks (persistent grid)

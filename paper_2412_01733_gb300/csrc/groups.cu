@@ -4,12 +4,14 @@
 // consecutive particles i-1, i that do not share the cell `delta` levels
 // above the finer of their two leaves:
 //   P(i-1, i) < max(leaf_level(i-1), leaf_level(i)) - delta,
-// P = number of leading octal digits the two keys share (21 if equal).
-// Neighbours in a group are then close on the scale of their own leaves, and
-// every group fits in the cell delta levels above its coarsest leaf.  This
-// keeps a chunk that jumps between distant parts of the Morton curve, or
-// from a dense region into a sparse one, from turning its walk into a
-// near-direct sum.  delta = 0 keeps plain chunks.
+// P = number of leading octal digits the two keys share (21 if equal), and
+// where their smallest common cell (level P) holds more than cmax = 128 Gs
+// particles.  Neighbours in a group are then close on the scale of their own
+// leaves, every group fits in the cell delta levels above its coarsest leaf,
+// and in a cell of at most cmax particles.  This keeps a chunk that jumps
+// between distant parts of the Morton curve, or a sparse group whose box
+// would enclose a dense region, from turning its walk into a near-direct
+// sum.  delta = 0 keeps plain chunks (no cuts at all).
 // Output: gfirst[0..ng] (group g = sorted particles [gfirst[g], gfirst[g+1]))
 // and the group count in the counter block.
 #include "common.cuh"
@@ -20,32 +22,47 @@ constexpr int kGScanThreads = 256;
 constexpr int kGScanItems = 8;
 constexpr int kGScanTile = kGScanThreads * kGScanItems;
 
-// leaf level of every sorted particle
+// leaf level and leaf node of every sorted particle
 __global__ void __launch_bounds__(256) k_leaf_levels(const uint32_t *__restrict__ ctr, const uint4 *__restrict__ ngeo,
-                                                     const uint2 *__restrict__ nlink, uint8_t *__restrict__ plev) {
+                                                     const uint2 *__restrict__ nlink, uint8_t *__restrict__ plev,
+                                                     uint32_t *__restrict__ pleaf) {
     const uint32_t nn = ctr[kCtrLevelStart + kLevels];
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nn; c += gridDim.x * blockDim.x) {
         const uint4 g = ngeo[c];
         if (!((g.w >> 8) & 1u)) continue;
         const uint2 l = nlink[c];
         const uint8_t lv = (uint8_t)(g.w & 0xffu);
-        for (uint32_t s = l.x; s < l.x + l.y; ++s) plev[s] = lv;
+        for (uint32_t s = l.x; s < l.x + l.y; ++s) {
+            plev[s] = lv;
+            pleaf[s] = c;
+        }
     }
 }
 
 __device__ __forceinline__ bool group_starts(const uint64_t *__restrict__ skey, const uint8_t *__restrict__ plev,
-                                             int64_t i, int64_t s0, int delta) {
+                                             const uint32_t *__restrict__ pleaf, const uint32_t *__restrict__ nparent,
+                                             const uint32_t *__restrict__ ncount, int64_t i, int64_t s0, int delta,
+                                             uint32_t cmax) {
     if (i == s0) return true;
     if (delta <= 0) return false;
     const uint64_t d = skey[i - 1] ^ skey[i];
     const int shared = d ? (62 - (63 - __clzll((long long)d))) / 3 : kMaxLevel;
     const int lmax = max((int)plev[i - 1], (int)plev[i]);
-    return shared < lmax - delta;
+    if (shared < lmax - delta) return true;
+    // smallest common cell: the ancestor of i's leaf at level `shared` (at most
+    // delta steps up here); when i's leaf is already no finer than that level,
+    // both particles share the leaf and it bounds the population from above
+    uint32_t node = pleaf[i];
+    for (int lv = plev[i]; lv > shared; --lv) node = nparent[node];
+    return ncount[node] > cmax;
 }
 
 // One warp per chunk: number of groups that start inside it.
 template <bool WRITE>
 __global__ void __launch_bounds__(256) k_group_chunks(const uint64_t *__restrict__ skey, const uint8_t *__restrict__ plev,
+                                                      const uint32_t *__restrict__ pleaf,
+                                                      const uint32_t *__restrict__ nparent,
+                                                      const uint32_t *__restrict__ ncount, uint32_t cmax,
                                                       int64_t n, int gs, int delta, int64_t nchunks,
                                                       uint32_t *__restrict__ ccount, const uint32_t *__restrict__ coff,
                                                       uint32_t *__restrict__ gfirst, const uint32_t *__restrict__ ctr) {
@@ -58,7 +75,8 @@ __global__ void __launch_bounds__(256) k_group_chunks(const uint64_t *__restrict
     uint32_t total = 0;
     for (int64_t off = 0; off < gs; off += 32) {
         const int64_t i = s0 + off + lane;
-        const bool st = off + lane < gs && i < s1 && group_starts(skey, plev, i, s0, delta);
+        const bool st = off + lane < gs && i < s1 &&
+                        group_starts(skey, plev, pleaf, nparent, ncount, i, s0, delta, cmax);
         const uint32_t b = __ballot_sync(0xffffffffu, st);
         if (WRITE && st) gfirst[base + total + __popc(b & lanemask_lt())] = (uint32_t)i;
         total += __popc(b);
@@ -102,14 +120,16 @@ cudaError_t launch_groups(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
     const int64_t tiles = (nchunks + kGScanTile - 1) / kGScanTile;
     cudaError_t e = cudaMemsetAsync(ws->gscan_status, 0, (size_t)tiles * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    k_leaf_levels<<<grid_for(ws->node_cap, 256, 152 * 8), 256, 0, s>>>(ws->ctr, ws->ngeo, ws->nlink, ws->plev);
+    k_leaf_levels<<<grid_for(ws->node_cap, 256, 152 * 8), 256, 0, s>>>(ws->ctr, ws->ngeo, ws->nlink, ws->plev,
+                                                                        ws->pleaf);
     const unsigned wb = (unsigned)((nchunks * 32 + 255) / 256);
-    k_group_chunks<false><<<wb, 256, 0, s>>>(ws->key, ws->plev, n, gs, ws->p.group_split, nchunks, ws->ccount,
-                                            nullptr, nullptr, ws->ctr);
+    const uint32_t cmax = 128u * (uint32_t)gs;
+    k_group_chunks<false><<<wb, 256, 0, s>>>(ws->key, ws->plev, ws->pleaf, ws->nparent, ws->ncount, cmax, n, gs,
+                                            ws->p.group_split, nchunks, ws->ccount, nullptr, nullptr, ws->ctr);
     k_group_scan<<<(unsigned)tiles, kGScanThreads, 0, s>>>(ws->ccount, ws->coff, nchunks, ws->gscan_status, ws->ctr,
                                                           ws->dstatus);
-    k_group_chunks<true><<<wb, 256, 0, s>>>(ws->key, ws->plev, n, gs, ws->p.group_split, nchunks, nullptr, ws->coff,
-                                           ws->gfirst, ws->ctr);
+    k_group_chunks<true><<<wb, 256, 0, s>>>(ws->key, ws->plev, ws->pleaf, ws->nparent, ws->ncount, cmax, n, gs,
+                                           ws->p.group_split, nchunks, nullptr, ws->coff, ws->gfirst, ws->ctr);
     ws->launches += 4;
     return cudaGetLastError();
 }

@@ -81,9 +81,10 @@ def test_tree_leapfrog_gradient_parity(orc, precision, tol):
 def test_tree_leapfrog_fd_unfrozen():
     """The adjoint config in miniature (Plummer, eps = 0.01, theta = 0.7, 16
     steps, checkpoints every 4, FP64): central FD (h = 1e-6) of the full GPU
-    map, tree rebuilt every step, on 32 coordinates.  A perturbation that moves
-    a particle across a cell boundary changes the structure and the map jumps;
-    at least 28 of 32 coordinates must match the frozen-structure gradient."""
+    map, tree rebuilt every step, on 32 coordinates (mass steps relative, 1e-4).
+    A perturbation that moves a particle across a cell boundary changes the
+    structure and the map jumps; at least 28 of 32 coordinates must match the
+    frozen-structure gradient to 1e-5 plus the finite-difference round-off."""
     tg = _tg()
     from paper_2412_01733_gb300.autograd import TreeLeapfrog
     n, K, tau, nsel = 8192, 16, 0.01, 1024
@@ -106,6 +107,7 @@ def test_tree_leapfrog_fd_unfrozen():
     rng = np.random.default_rng(3)
     ok = 0
     x0, v0, m0 = xg.detach(), vg.detach(), mg.detach()
+    L0 = loss.item()
     for k in range(32):
         which, d, i = k % 3, int(rng.integers(0, 3)), int(rng.integers(0, n))
         if which == 2:
@@ -118,5 +120,7 @@ def test_tree_leapfrog_fd_unfrozen():
             bp = base.clone(); bp[d, i] += h; bn = base.clone(); bn[d, i] -= h
             fd = ((L(bp, v0, m0) - L(bn, v0, m0)) if which == 0 else (L(x0, bp, m0) - L(x0, bn, m0))) / (2 * h)
             g = (xg.grad if which == 0 else vg.grad)[d, i].item()
-        ok += abs(fd - g) <= 1e-5 * max(abs(fd), 1e-3)
+        # central-difference round-off: a few ulps of the loss divided by 2h
+        noise = 20 * 2.2e-16 * abs(L0) / (2 * h)
+        ok += abs(fd - g) <= 1e-5 * abs(g) + noise
     assert ok >= 28, ok

@@ -219,14 +219,16 @@ def _octal_digits(key):
     return [(int(key) >> (3 * (20 - i))) & 7 for i in range(21)]
 
 
-@pytest.mark.parametrize("kind,n,gs,lcap,delta", [("plummer", 3000, 32, 16, 3), ("galaxy", 4000, 32, 8, 2),
-                                                  ("galaxy", 2000, 64, 4, 1), ("plummer", 1000, 16, 1, 3),
-                                                  ("plummer", 500, 32, 16, 0)])
-def test_groups_rule(orc, kind, n, gs, lcap, delta):
+@pytest.mark.parametrize("kind,n,gs,lcap,delta,cmax", [("plummer", 3000, 32, 16, 3, 4096), ("galaxy", 4000, 32, 8, 2, 256),
+                                                       ("galaxy", 2000, 64, 4, 1, 0), ("plummer", 1000, 16, 1, 3, 64),
+                                                       ("plummer", 500, 32, 16, 0, 0), ("plummer", 3000, 32, 16, 0, 128)])
+def test_groups_rule(orc, kind, n, gs, lcap, delta, cmax):
     """Walk groups: chunks of gs in key order, cut between neighbours that do
-    not share the cell delta levels above the finer of their leaves.
-    Checked by counting shared octal digits directly, with leaf levels from
-    a scan of the leaves, and through the box bound the rule implies."""
+    not share the cell delta levels above the finer of their leaves, or whose
+    smallest common cell holds more than cmax particles.  Checked by counting
+    shared octal digits directly, with leaf levels from a scan of the leaves and
+    cell populations from counting equal key prefixes, and through the two
+    bounds the rule implies."""
     x, _, _ = (inputs.plummer if kind == "plummer" else inputs.galaxy)(n, 29)
     x = x.numpy()
     lo, k = orc.box(x)
@@ -234,32 +236,44 @@ def test_groups_rule(orc, kind, n, gs, lcap, delta):
     perm = orc.sort(key)
     sk = key[perm]
     t = orc.octree(sk, lcap)
-    gf = orc.groups(sk, t, gs, delta)
+    gf = orc.groups(sk, t, gs, delta, cmax)
     leaf_level = np.full(n, -1)
     for c in np.nonzero(t.nchild == 0)[0]:
         leaf_level[t.first[c]: t.first[c] + t.count[c]] = t.level[c]
     assert np.all(leaf_level >= 0)
-    want = [0]
     digits = [_octal_digits(v) for v in sk]
+    prefixes = [tuple(dd) for dd in digits]
+
+    def population(i, lvl):
+        return sum(1 for p in prefixes if p[:lvl] == prefixes[i][:lvl])
+
+    want = [0]
     for i in range(1, n):
         shared = 21
         for j in range(21):
             if digits[i][j] != digits[i - 1][j]:
                 shared = j
                 break
-        if i % gs == 0 or (delta > 0 and shared < max(leaf_level[i], leaf_level[i - 1]) - delta):
+        cut = i % gs == 0 or (delta > 0 and shared < max(leaf_level[i], leaf_level[i - 1]) - delta)
+        if not cut and cmax > 0 and population(i, shared) > cmax:
+            cut = True
+        if cut:
             want.append(i)
     np.testing.assert_array_equal(gf, want + [n])
     sizes = np.diff(gf)
     assert sizes.min() >= 1 and sizes.max() <= gs
-    if delta == 0:
+    if delta == 0 and cmax == 0:
         assert len(gf) - 1 == (n + gs - 1) // gs
     qs = q[:, perm]
     for g in range(len(gf) - 1):
         a, b = gf[g], gf[g + 1]
-        lvl = max(0, leaf_level[a:b].min() - delta) if delta > 0 else 0
-        cell = (qs[:, a:b] >> (21 - lvl))
-        assert np.all(cell == cell[:, :1]), (g, lvl)     # the group fits one cell of that level
+        if delta > 0:
+            lvl = max(0, leaf_level[a:b].min() - delta)
+            cell = (qs[:, a:b] >> (21 - lvl))
+            assert np.all(cell == cell[:, :1]), (g, lvl)     # fits one cell of that level
+        if cmax > 0 and b - a > 1:
+            common = min(next((j for j in range(21) if digits[a][j] != digits[b - 1][j]), 21), 21)
+            assert population(a, common) <= cmax              # its smallest cell is small
 
 
 # ---------------------------------------------------------------- forces
