@@ -60,10 +60,13 @@ def _args():
                     help="particles of the oracle's bounded sample (same galaxy recipe)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the main leg only (no FP64 leg, error check, e2e, CPU baseline)")
-    ap.add_argument("--study", choices=["theta", "threads"], default=None,
+    ap.add_argument("--study", choices=["theta", "threads", "ensemble", "adjoint"], default=None,
                     help="theta: precision study on the Plummer N=2^20 config (force error vs direct sum, "
                          "energy drift, FP32 vs FP64 time per force, theta in {0.4,0.5,0.7,1.0}); "
-                         "threads: T(M), speedup and efficiency of the CPU oracle vs host threads M")
+                         "threads: T(M), speedup and efficiency of the CPU oracle vs host threads M; "
+                         "ensemble: 512 Plummer clusters in one build, autotuned, one CUDA graph per step; "
+                         "adjoint: gradients through 16 KDK steps of Plummer N=262144 (times, FP32 vs FP64, "
+                         "tree vs theta=0, finite differences)")
     ap.add_argument("--study-steps", type=int, default=100)
     return ap.parse_args()
 
@@ -435,10 +438,180 @@ def study_threads(a):
         O.set_threads(ncpu)
 
 
+def study_ensemble(a):
+    """Ensemble configuration: 512 independent Plummer clusters (a = 1, M = 1 each), sizes
+    N_c = floor(exp U(ln 1024, ln 65536)) (about 7.9e6 particles in all), eps = 0.01, theta = 0.6,
+    quadrupole, FP32 + Kahan, KDK tau = 0.005.  The autotuner picks (leaf_cap, group_size,
+    stack_depth); each step is then one CUDA graph launch (leapfrog step + diagnostics).  Reports
+    particles/s and interactions/s of the step, the same steps launched eagerly, and the per-cluster
+    relative energy drift over all steps run (median, max)."""
+    import numpy as np
+    import torch
+
+    from paper_2412_01733_gb300 import build, inputs, treegb
+    build.build()
+    B, tau = 512, 0.005
+    x, v, m, off = inputs.ensemble(B, SEED, device="cuda", dtype=torch.float32)
+    x, v, m = x.contiguous(), v.contiguous(), m.contiguous()
+    n = x.shape[1]
+    base = dict(eps=0.01, theta=0.6, order=2, kahan=1, leaf_cap=16, group_size=32)
+    t0 = time.perf_counter()
+    best, table = treegb.autotune(x, m, offsets=off, reps=3, **base)
+    tune_s = time.perf_counter() - t0
+    p = dict(base, leaf_cap=best.leaf_cap, group_size=best.group_size, stack_depth=best.stack_depth)
+    ws = treegb.Workspace(n, **p)
+    ws.set_segments(off)
+    acc, phi = ws.accel(x, m)
+    d0 = ws.diagnostics_segments(x, v, m, phi).cpu().numpy()
+    diag = torch.zeros(8, dtype=torch.float64, device="cuda")
+    ws.graph_capture(x, v, m, acc, tau, phi=phi, diag=diag)
+    s = torch.cuda.current_stream()
+
+    def timed(fn, k):
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(); e0.record(s)
+        for _ in range(k):
+            fn()
+        e1.record(s); torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    K, W = a.study_steps, max(3, a.warmup)
+    for _ in range(W):
+        ws.graph_launch()
+    l0 = ws.launches()
+    ms_graph = timed(ws.graph_launch, K)
+    launches_per_step = (ws.launches() - l0) / K
+    inf = ws.info()
+
+    def eager():
+        ws.leapfrog_step(x, v, m, acc, tau, phi=phi)
+        ws.diagnostics(x, v, m, phi, out=diag)
+    ms_eager = timed(eager, max(3, K // 5))
+    steps_run = W + K + max(3, K // 5)
+    d1 = ws.diagnostics_segments(x, v, m, phi).cpu().numpy()
+    e0_, e1_ = d0[:, 0] + d0[:, 1], d1[:, 0] + d1[:, 1]
+    drift = np.abs(e1_ - e0_) / np.abs(e0_)
+    row = {"study": "ensemble", "clusters": B, "n": n, "eps": 0.01, "theta": 0.6, "order": "quadrupole",
+           "dtype": "f32+kahan", "tau": tau, "autotuned": {"leaf_cap": best.leaf_cap, "group_size": best.group_size,
+                                                           "stack_depth": best.stack_depth},
+           "autotune_table": [list(r) for r in table], "autotune_s": tune_s,
+           "graph": {"ms_per_step": ms_graph, "particles_per_s": n / (ms_graph / 1e3),
+                     "interactions_per_s": (inf["pp_pairs"] + inf["pc_pairs"]) / (ms_graph / 1e3),
+                     "kernels_per_step": launches_per_step, "steps": K},
+           "eager": {"ms_per_step": ms_eager, "particles_per_s": n / (ms_eager / 1e3)},
+           "interactions_per_particle": (inf["pp_pairs"] + inf["pc_pairs"]) / n, "n_groups": inf["n_groups"],
+           "energy_drift_per_cluster": {"median": float(np.median(drift)), "max": float(drift.max()),
+                                        "steps": steps_run},
+           "status": ws.status()}
+    print(json.dumps(row), flush=True)
+
+
+def study_adjoint(a):
+    """Adjoint configuration: Plummer N = 262,144, eps = 0.01, theta = 0.7, quadrupole, K = 16 KDK steps of
+    tau = 0.01, checkpoints every 4; loss = sum over the first 1024 particles (caller order) of |x_i^K|^2 + W_K.
+    Reports forward and backward times in FP32 and FP64 (and their ratio), the FP32 gradient against the FP64
+    one, the theta = 0.7 gradient against the theta = 0 one (every pair exact: the gradient of the direct-sum
+    map, FP32), and central differences (h = 1e-6; masses relative 1e-4) of the FP64 GPU map, tree rebuilt
+    every step, on 32 coordinates, with the fraction whose perturbation changed the tree structure (node,
+    group or pair counts of any step)."""
+    import numpy as np
+    import torch
+
+    from paper_2412_01733_gb300 import build, inputs, treegb
+    from paper_2412_01733_gb300.autograd import TreeLeapfrog
+    build.build()
+    n, K, tau, nsel, ck = 262144, 16, 0.01, 1024, 4
+    x0, v0, m0 = inputs.plummer(n, SEED, device="cuda", dtype=torch.float64)
+
+    def grads(dt, theta):
+        ws = treegb.Workspace(n, eps=0.01, theta=theta, order=2, precision="f64" if dt == torch.float64 else "f32")
+        x = x0.to(dt).clone().requires_grad_(True)
+        v = v0.to(dt).clone().requires_grad_(True)
+        m = m0.to(dt).clone().requires_grad_(True)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize(); e[0].record()
+        xK, vK, WK = TreeLeapfrog.apply(x, v, m, ws, K, tau, ck)
+        loss = (xK[:, :nsel].double() ** 2).sum() + WK
+        e[1].record()
+        loss.backward()
+        e[2].record(); torch.cuda.synchronize()
+        st = ws.status()
+        out = dict(loss=float(loss), fwd_ms=e[0].elapsed_time(e[1]), bwd_ms=e[1].elapsed_time(e[2]), status=st)
+        g = [t.grad.double() for t in (x, v, m)]
+        del ws
+        torch.cuda.empty_cache()
+        return out, g
+
+    def cmp(g, ref):
+        res = {}
+        for name, a_, b_ in zip(("x", "v", "m"), g, ref):
+            d = (a_ - b_).abs()
+            sc = b_.abs().max()
+            big = b_.abs() > 1e-3 * sc
+            res[name] = {"max_abs_over_max": float(d.max() / sc),
+                         "median_rel": float((d[big] / b_.abs()[big]).median())}
+        return res
+
+    row = {"study": "adjoint", "n": n, "steps": K, "tau": tau, "eps": 0.01, "theta": 0.7, "checkpoint_every": ck,
+           "loss": "sum_{i<1024} |x_i^K|^2 + W_K"}
+    r32, g32 = grads(torch.float32, 0.7)
+    r64, g64 = grads(torch.float64, 0.7)
+    r0, g0 = grads(torch.float32, 0.0)
+    row["f32"] = dict(r32, bwd_over_fwd=r32["bwd_ms"] / r32["fwd_ms"])
+    row["f64"] = dict(r64, bwd_over_fwd=r64["bwd_ms"] / r64["fwd_ms"])
+    row["theta0_f32"] = dict(r0, bwd_over_fwd=r0["bwd_ms"] / r0["fwd_ms"])
+    row["f32_vs_f64"] = cmp(g32, g64)
+    row["tree_vs_theta0"] = cmp(g32, g0)
+
+    ws = treegb.Workspace(n, eps=0.01, theta=0.7, order=2, precision="f64")
+
+    def L(xx, vv, mm):
+        xx, vv = xx.clone(), vv.clone()
+        acc, phi = ws.accel(xx, mm)
+        sig = []
+        for _ in range(K):
+            ws.leapfrog_step(xx, vv, mm, acc, tau, phi=phi)
+            inf = ws.info()
+            sig.append((inf["n_nodes"], inf["n_groups"], inf["pp_pairs"], inf["pc_pairs"]))
+        return float((xx[:, :nsel] ** 2).sum() + ws.diagnostics(xx, vv, mm, phi)[1]), sig
+
+    L0, sig0 = L(x0, v0, m0)
+    rng = np.random.default_rng(3)
+    ok = changed = 0
+    rows = []
+    for k in range(32):
+        which, d, i = k % 3, int(rng.integers(0, 3)), int(rng.integers(0, n))
+        if which == 2:
+            h = 1e-4 * float(m0[i])
+            mp = m0.clone(); mp[i] += h; mn = m0.clone(); mn[i] -= h
+            (Lp, sp), (Ln, sn) = L(x0, v0, mp), L(x0, v0, mn)
+            g = float(g64[2][i])
+        else:
+            h = 1e-6
+            base = x0 if which == 0 else v0
+            bp = base.clone(); bp[d, i] += h; bn = base.clone(); bn[d, i] -= h
+            (Lp, sp), (Ln, sn) = (L(bp, v0, m0), L(bn, v0, m0)) if which == 0 else (L(x0, bp, m0), L(x0, bn, m0))
+            g = float(g64[which][d, i])
+        fd = (Lp - Ln) / (2 * h)
+        noise = 20 * 2.2e-16 * abs(L0) / (2 * h)
+        good = abs(fd - g) <= 1e-5 * abs(g) + noise
+        ch = sp != sig0 or sn != sig0
+        ok += good; changed += ch
+        rows.append({"coord": ["x", "v", "m"][which], "d": d, "i": i, "fd": fd, "grad": g, "match": bool(good),
+                     "structure_changed": bool(ch)})
+    row["fd_unfrozen_f64"] = {"coordinates": 32, "match_1e-5": ok, "structure_changed": changed,
+                              "loss": L0, "detail": rows}
+    print(json.dumps(row), flush=True)
+
+
 def main():
     a = _args()
     if a.study == "theta":
         return study_theta(a)
+    if a.study == "adjoint":
+        return study_adjoint(a)
+    if a.study == "ensemble":
+        return study_ensemble(a)
     if a.study == "threads":
         return study_threads(a)
     if a.impl == "reference":

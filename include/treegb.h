@@ -118,7 +118,8 @@ typedef struct {
     int64_t n_groups;           /* walk groups of the last tree */
     int64_t list_pc;            /* stored PC list entries (TREE_FLAG_EMIT_LISTS) */
     int64_t list_pp;            /* stored PP leaf entries (TREE_FLAG_EMIT_LISTS) */
-    int64_t launches;           /* CUDA kernels this workspace has launched so far */
+    int64_t launches;           /* CUDA kernels this workspace has launched so far (this call included) */
+    int64_t n_segments;         /* independent systems (tree_set_segments); 1 = a single system */
 } TreeInfo;
 
 /* Phases timed by tree_timing_read (indices into its ms[] output). */
@@ -152,6 +153,21 @@ tree_status_t tree_workspace_destroy(TreeWorkspace *ws);
  * (TREE_ERR_ARG otherwise).  A changed leaf_cap needs a new workspace. */
 tree_status_t tree_set_params(TreeWorkspace *ws, const TreeParams *p);
 tree_status_t tree_get_params(const TreeWorkspace *ws, TreeParams *p);
+
+/* Ensembles (not in the paper, which treats one system): declares that the
+ * n = offsets[nseg] particles form nseg independent systems, system b being
+ * the caller's particles [offsets[b], offsets[b+1]) (host int64[nseg + 1],
+ * offsets[0] = 0, strictly increasing: no empty system; 2 <= nseg <= 65536).
+ * Every later build, force and step call treats each system exactly as if
+ * it were alone: its own box, keys, octree (its root is node b of level 0),
+ * walk groups and walk; there are no forces between systems.  Sorted
+ * positions of system b are [offsets[b], offsets[b+1]).  Calls must then pass
+ * n = offsets[nseg] (TREE_ERR_ARG otherwise).  nseg = 0 or 1 returns to a
+ * single system of any n.  Synchronises the device; drops any captured step
+ * and the stored tree.  Errors: TREE_ERR_ARG, TREE_ERR_CAPACITY (n > n_max),
+ * TREE_ERR_ALLOC. */
+tree_status_t tree_set_segments(TreeWorkspace *ws, int64_t nseg, const int64_t *offsets);
+tree_status_t tree_get_segments(const TreeWorkspace *ws, int64_t *nseg);
 
 /* Steps box, keys, sort, octree of the canonical tree (Sec. 2).
  * x: [3][n] positions of dtype (must equal the workspace precision).  The
@@ -220,6 +236,41 @@ tree_status_t leapfrog_step(TreeWorkspace *ws, void *x, void *v, const void *m, 
  * out: device double[8].  Deterministic (fixed reduction order). */
 tree_status_t tree_diagnostics(TreeWorkspace *ws, const void *x, const void *v, const void *m,
                                const void *phi, int64_t n, double *out, void *stream);
+
+/* tree_diagnostics per system of the ensemble: out device double[nseg][8].
+ * With a single system it equals tree_diagnostics. */
+tree_status_t tree_diagnostics_segments(TreeWorkspace *ws, const void *x, const void *v, const void *m,
+                                        const void *phi, int64_t n, double *out, void *stream);
+
+/* CUDA graph of one step: captures leapfrog_step(ws, x, v, m, a, phi, tau,
+ * n) -- and, when diag is non-NULL, tree_diagnostics into diag (device
+ * double[8]) -- on an internal stream; nothing runs.  Every
+ * leapfrog_graph_launch then replays that step with the same pointers and
+ * parameters as one graph launch on the caller's stream.  A new capture, a
+ * tree_set_params or a tree_set_segments drops the graph.  Synchronises the
+ * device.  Errors: as leapfrog_step; TREE_ERR_CUDA if capture fails. */
+tree_status_t leapfrog_graph_capture(TreeWorkspace *ws, void *x, void *v, const void *m, void *a, void *phi,
+                                     double tau, int64_t n, double *diag);
+/* TREE_ERR_STATE if no step has been captured. */
+tree_status_t leapfrog_graph_launch(TreeWorkspace *ws, void *stream);
+
+/* Autotuner: times one force evaluation (tree_build + tree_moments +
+ * tree_forces, `reps` times after one untimed run) on the caller's x, m
+ * ([3][n], [n] of base->precision; with nseg > 1 the ensemble given by
+ * offsets as in tree_set_segments) for every leaf_cap in {4, 8, 16},
+ * group_size in {16, 32, 64} and stack_depth in {512, 1024}, the other
+ * parameters taken from base, each leaf_cap in a temporary workspace of
+ * n_max = n.  *best = the fastest candidate whose walks set no device status
+ * bit.  table (host double[*ncand][4], may be NULL): rows (leaf_cap,
+ * group_size, stack_depth, ms per evaluation; inf if rejected); *ncand in:
+ * rows available, out: candidates tried.  Synchronises the device. */
+tree_status_t tree_autotune(const TreeParams *base, int64_t nseg, const int64_t *offsets, const void *x,
+                            const void *m, int64_t n, int32_t reps, TreeParams *best, double *table,
+                            int32_t *ncand, void *stream);
+
+/* Boxes of the last build, one per system: lo host double[nseg][3], k host
+ * int32[nseg] (L = 2^k); either may be NULL.  Synchronises the device. */
+tree_status_t tree_export_boxes(TreeWorkspace *ws, double *lo, int32_t *k);
 
 /* Direct summation of Eq. 1 on the GPU, j != i, for nt targets (indices into
  * x, device int64[nt]) against all n sources.  dtype TREE_F32: FP32 pair terms,

@@ -245,6 +245,31 @@ def tree_accel(x, m, **kw):
 
 
 # --------------------------------------------------------------------------- #
+# Ensembles (not in the paper): independent systems, system b = particles
+# [offsets[b], offsets[b+1]).  By definition each is treated exactly as if it
+# were alone -- its own box, keys, tree, groups and lists -- and systems exert
+# no force on one another.
+def ensemble_tree_forces(x, m, offsets, **kw):
+    """tree_forces of every system alone; returns (a, phi) in the caller's order
+    and the list of per-system TreeResults."""
+    x = _f64(x); m = _f64(m)
+    n = m.shape[0]
+    offsets = [int(o) for o in offsets]
+    assert offsets[0] == 0 and offsets[-1] == n and all(b > a for a, b in zip(offsets, offsets[1:]))
+    a = np.zeros((3, n)); phi = np.zeros(n); rs = []
+    for b0, b1 in zip(offsets[:-1], offsets[1:]):
+        r = tree_forces(x[:, b0:b1], m[b0:b1], **kw)
+        a[:, b0:b1] = r.a; phi[b0:b1] = r.phi
+        rs.append(r)
+    return a, phi, rs
+
+
+def ensemble_accel(x, m, offsets, **kw):
+    a, phi, _ = ensemble_tree_forces(x, m, offsets, **kw)
+    return a, phi
+
+
+# --------------------------------------------------------------------------- #
 # Eqs. 2-5: kick-drift-kick leapfrog, a^0 computed once before the first step.
 def kdk(x, v, m, tau, nsteps, accel, a0=None):
     """Run nsteps of Eqs. 2-5.  accel(x) -> (a, phi).  Returns x, v, a, phi."""

@@ -72,9 +72,17 @@ void free_all(TreeWorkspace *ws) {
                     ws->mom64, ws->mom_a, ws->mom_b, ws->mom_c, ws->dstatus, ws->stats, ws->gstat,
                     ws->list_cnt, ws->pc_list, ws->pp_list, ws->direct_part, ws->dmac, ws->gorder,
                     ws->gkey, ws->gbucket, ws->gfirst, ws->plev, ws->ccount, ws->coff, ws->gscan_status,
-                    ws->adj_cot, ws->adj_xt, ws->adj_xg, ws->adj_mg, ws->adj_ccot, ws->pleaf, ws->nparent};
+                    ws->adj_cot, ws->adj_xt, ws->adj_xg, ws->adj_mg, ws->adj_ccot, ws->pleaf, ws->nparent,
+                    ws->seg_off, ws->seg_cstart, ws->seg_bchunk, ws->seg_bfirst, ws->seg_part,
+                    ws->seg_digit_off};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (ws->graph_exec) cudaGraphExecDestroy(ws->graph_exec);
+    if (ws->graph) cudaGraphDestroy(ws->graph);
+    if (ws->cap_stream) cudaStreamDestroy(ws->cap_stream);
+    ws->graph_exec = nullptr;
+    ws->graph = nullptr;
+    ws->cap_stream = nullptr;
     for (cudaEvent_t e : ws->ev) cudaEventDestroy(e);
     ws->ev.clear();
     ws->ev_phase.clear();
@@ -113,6 +121,60 @@ struct PhaseScope {
         ws->timed_launches += ws->launches - l0;
     }
 };
+
+// Release the segment tables (back to a single system of any n).
+void free_segments(TreeWorkspace *ws) {
+    void *ptrs[] = {ws->seg_off, ws->seg_cstart, ws->seg_bchunk, ws->seg_bfirst, ws->seg_part, ws->seg_digit_off};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    ws->seg_off = nullptr;
+    ws->seg_cstart = nullptr;
+    ws->seg_bchunk = nullptr;
+    ws->seg_bfirst = nullptr;
+    ws->seg_part = nullptr;
+    ws->seg_digit_off = nullptr;
+    ws->seg_off_h.clear();
+    ws->nseg = 1;
+    ws->seg_passes = 0;
+    ws->seg_nbchunk = 0;
+    ws->seg_nchunks = 0;
+    ws->seg_cstart_gs = 0;
+}
+
+void drop_graph(TreeWorkspace *ws) {
+    if (ws->graph_exec) cudaGraphExecDestroy(ws->graph_exec);
+    if (ws->graph) cudaGraphDestroy(ws->graph);
+    ws->graph_exec = nullptr;
+    ws->graph = nullptr;
+    ws->graph_launches = 0;
+}
+
+// First Gs chunk of every segment for the current group size (synchronous
+// upload; called when the segments or the group size change, never inside
+// a step, so that a step stays free of host synchronisation).
+tree_status_t upload_seg_chunks(TreeWorkspace *ws) {
+    if (ws->nseg <= 1 || ws->seg_cstart_gs == ws->p.group_size) return TREE_OK;
+    const int64_t gs = ws->p.group_size;
+    std::vector<uint32_t> cs((size_t)ws->nseg + 1);
+    int64_t c = 0;
+    for (int64_t b = 0; b < ws->nseg; ++b) {
+        cs[b] = (uint32_t)c;
+        c += (ws->seg_off_h[b + 1] - ws->seg_off_h[b] + gs - 1) / gs;
+    }
+    cs[ws->nseg] = (uint32_t)c;
+    TRY_CUDA(cudaMemcpy(ws->seg_cstart, cs.data(), cs.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    ws->seg_nchunks = c;
+    ws->seg_cstart_gs = ws->p.group_size;
+    return TREE_OK;
+}
+
+// Step and build calls: n must match the segments when they are set.
+tree_status_t check_n(const TreeWorkspace *ws, int64_t n) {
+    if (n < 0) return TREE_ERR_ARG;
+    if (n > ws->n_max) return TREE_ERR_CAPACITY;
+    if (ws->nseg > 1 && n != ws->seg_off_h[ws->nseg]) return TREE_ERR_ARG;
+    return TREE_OK;
+}
 
 tree_status_t upload_mac(TreeWorkspace *ws, cudaStream_t s) {
     if (ws->mac_theta != ws->p.theta) {
@@ -189,7 +251,7 @@ tree_status_t tree_workspace_create(int64_t n_max, const TreeParams *p, TreeWork
     const size_t v2 = p->precision == TREE_F64 ? sizeof(double2a) : sizeof(float2);
     bool ok = dalloc(&ws->key, N) && dalloc(&ws->key_alt, N) && dalloc(&ws->idx, N) && dalloc(&ws->idx_alt, N) &&
               dalloc(&ws->hist, 2 * kSortPasses * kRadix) &&
-              dalloc(&ws->sort_status, (size_t)kSortPasses * ws->sort_tiles_max * kRadix) &&
+              dalloc(&ws->sort_status, (size_t)(kSortPasses + kSegPassesMax) * ws->sort_tiles_max * kRadix) &&
               dalloc(&ws->level_status, (size_t)kLevels * ws->level_tiles_max) && dalloc(&ws->ctr, kCtrCount) &&
               dalloc(&ws->part, (size_t)kMaxBlocksReduce * 8) && dalloc(&ws->box, 1) &&
               dalloc((unsigned char **)&ws->spos, N * v4) && dalloc(&ws->nfirst, NC) && dalloc(&ws->ncount, NC) &&
@@ -203,6 +265,8 @@ tree_status_t tree_workspace_create(int64_t n_max, const TreeParams *p, TreeWork
               dalloc(&ws->ccount, (size_t)chunks_max) && dalloc(&ws->coff, (size_t)chunks_max) &&
               dalloc(&ws->gscan_status, (size_t)(chunks_max / 2048 + 2)) &&
               dalloc(&ws->dmac, kLevels);
+    ws->chunks_cap = chunks_max;
+    ws->box_cap = 1;
     if (!ok) {
         free_all(ws);
         delete ws;
@@ -236,12 +300,105 @@ tree_status_t tree_set_params(TreeWorkspace *ws, const TreeParams *p) {
     const int64_t keep_cap = ws->p.node_cap;
     ws->p = *p;
     ws->p.node_cap = keep_cap;
+    // a captured step holds the old parameters
+    drop_graph(ws);
     if (regroup) {
         // the walk groups come from the tree build: a new grouping needs a new build
         ws->list_groups = -1;
         ws->built = false;
         ws->has_moments = false;
+        TRY_CUDA(cudaDeviceSynchronize());
+        tree_status_t st2 = upload_seg_chunks(ws);
+        if (st2 != TREE_OK) return st2;
     }
+    return TREE_OK;
+}
+
+tree_status_t tree_set_segments(TreeWorkspace *ws, int64_t nseg, const int64_t *offsets) {
+    if (!ws) return TREE_ERR_ARG;
+    if (nseg < 0 || nseg > kMaxSegments) return TREE_ERR_ARG;
+    if (nseg > 1) {
+        if (!offsets || offsets[0] != 0) return TREE_ERR_ARG;
+        for (int64_t b = 0; b < nseg; ++b)
+            if (offsets[b + 1] <= offsets[b]) return TREE_ERR_ARG;
+        if (offsets[nseg] > ws->n_max) return TREE_ERR_CAPACITY;
+        if (nseg >= ws->node_cap) return TREE_ERR_CAPACITY;
+    }
+    // the tables below may be in use by queued work
+    TRY_CUDA(cudaDeviceSynchronize());
+    drop_graph(ws);
+    free_segments(ws);
+    ws->built = false;
+    ws->has_moments = false;
+    ws->list_groups = -1;
+    if (nseg <= 1) return TREE_OK;
+    const int64_t n = offsets[nseg];
+    // box chunks of at most kBoxChunk particles, never straddling segments
+    std::vector<uint4> bch;
+    std::vector<uint32_t> bfirst((size_t)nseg + 1);
+    for (int64_t b = 0; b < nseg; ++b) {
+        bfirst[b] = (uint32_t)bch.size();
+        for (int64_t i = offsets[b]; i < offsets[b + 1]; i += kBoxChunk) {
+            const int64_t e = i + kBoxChunk < offsets[b + 1] ? i + kBoxChunk : offsets[b + 1];
+            bch.push_back(make_uint4((uint32_t)i, (uint32_t)e, (uint32_t)b, 0u));
+        }
+    }
+    bfirst[nseg] = (uint32_t)bch.size();
+    // exclusive offsets of the segment-index digits (low byte, high byte)
+    std::vector<uint32_t> doff(2 * kRadix, 0u);
+    {
+        std::vector<int64_t> cnt(2 * kRadix, 0);
+        for (int64_t b = 0; b < nseg; ++b) {
+            const int64_t sz = offsets[b + 1] - offsets[b];
+            cnt[b & 0xff] += sz;
+            cnt[kRadix + ((b >> 8) & 0xff)] += sz;
+        }
+        for (int q = 0; q < 2; ++q) {
+            int64_t run = 0;
+            for (int d = 0; d < kRadix; ++d) {
+                doff[q * kRadix + d] = (uint32_t)run;
+                run += cnt[q * kRadix + d];
+            }
+        }
+    }
+    const int64_t chunks_need = (n + 15) / 16 + nseg + 1;
+    bool ok = dalloc(&ws->seg_off, (size_t)nseg + 1) && dalloc(&ws->seg_cstart, (size_t)nseg + 1) &&
+              dalloc(&ws->seg_bchunk, bch.size()) && dalloc(&ws->seg_bfirst, (size_t)nseg + 1) &&
+              dalloc(&ws->seg_part, bch.size() * 8) && dalloc(&ws->seg_digit_off, 2 * kRadix);
+    if (ok && nseg > ws->box_cap) {
+        cudaFree(ws->box);
+        ws->box = nullptr;
+        ok = dalloc(&ws->box, (size_t)nseg);
+        ws->box_cap = ok ? nseg : 0;
+    }
+    if (ok && chunks_need > ws->chunks_cap) {
+        cudaFree(ws->ccount);
+        cudaFree(ws->coff);
+        cudaFree(ws->gscan_status);
+        ws->ccount = ws->coff = ws->gscan_status = nullptr;
+        ok = dalloc(&ws->ccount, (size_t)chunks_need) && dalloc(&ws->coff, (size_t)chunks_need) &&
+             dalloc(&ws->gscan_status, (size_t)(chunks_need / 2048 + 2));
+        ws->chunks_cap = ok ? chunks_need : 0;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        free_segments(ws);
+        return TREE_ERR_ALLOC;
+    }
+    TRY_CUDA(cudaMemcpy(ws->seg_off, offsets, ((size_t)nseg + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    TRY_CUDA(cudaMemcpy(ws->seg_bchunk, bch.data(), bch.size() * sizeof(uint4), cudaMemcpyHostToDevice));
+    TRY_CUDA(cudaMemcpy(ws->seg_bfirst, bfirst.data(), bfirst.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    TRY_CUDA(cudaMemcpy(ws->seg_digit_off, doff.data(), doff.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    ws->seg_off_h.assign(offsets, offsets + nseg + 1);
+    ws->nseg = nseg;
+    ws->seg_passes = nseg <= 256 ? 1 : 2;
+    ws->seg_nbchunk = (int64_t)bch.size();
+    return upload_seg_chunks(ws);
+}
+
+tree_status_t tree_get_segments(const TreeWorkspace *ws, int64_t *nseg) {
+    if (!ws || !nseg) return TREE_ERR_ARG;
+    *nseg = ws->nseg;
     return TREE_OK;
 }
 
@@ -253,8 +410,8 @@ tree_status_t tree_get_params(const TreeWorkspace *ws, TreeParams *p) {
 
 tree_status_t tree_build(TreeWorkspace *ws, const void *x, int64_t n, int32_t dtype, void *stream) {
     if (!ws) return TREE_ERR_ARG;
-    if (n < 0) return TREE_ERR_ARG;
-    if (n > ws->n_max) return TREE_ERR_CAPACITY;
+    tree_status_t stn = check_n(ws, n);
+    if (stn != TREE_OK) return stn;
     if (dtype != ws->p.precision) return TREE_ERR_ARG;
     if (n > 0 && !x) return TREE_ERR_ARG;
     cudaStream_t s = as_stream(stream);
@@ -266,7 +423,7 @@ tree_status_t tree_build(TreeWorkspace *ws, const void *x, int64_t n, int32_t dt
     const int64_t tiles = (n + kSortTile - 1) / kSortTile;
     TRY_CUDA(cudaMemsetAsync(ws->ctr, 0, kCtrCount * sizeof(uint32_t), s));
     TRY_CUDA(cudaMemsetAsync(ws->hist, 0, kSortPasses * kRadix * sizeof(uint32_t), s));
-    for (int p = 0; p < kSortPasses; ++p)
+    for (int p = 0; p < kSortPasses + ws->seg_passes; ++p)
         TRY_CUDA(cudaMemsetAsync(ws->sort_status + (size_t)p * ws->sort_tiles_max * kRadix, 0,
                                  (size_t)tiles * kRadix * sizeof(uint32_t), s));
     TRY_CUDA(cudaMemsetAsync(ws->level_status, 0, (size_t)kLevels * ws->level_tiles_max * sizeof(uint32_t), s));
@@ -426,8 +583,9 @@ tree_status_t tree_accel(TreeWorkspace *ws, const void *x, const void *m, int64_
 tree_status_t leapfrog_step(TreeWorkspace *ws, void *x, void *v, const void *m, void *a, void *phi, double tau,
                             int64_t n, void *stream) {
     if (!ws) return TREE_ERR_ARG;
-    if (n < 0 || !isfinite(tau)) return TREE_ERR_ARG;
-    if (n > ws->n_max) return TREE_ERR_CAPACITY;
+    if (!isfinite(tau)) return TREE_ERR_ARG;
+    tree_status_t stn = check_n(ws, n);
+    if (stn != TREE_OK) return stn;
     if (n == 0) return TREE_OK;
     if (!x || !v || !m || !a) return TREE_ERR_ARG;
     cudaStream_t s = as_stream(stream);
@@ -438,7 +596,7 @@ tree_status_t leapfrog_step(TreeWorkspace *ws, void *x, void *v, const void *m, 
     const int64_t tiles = (n + kSortTile - 1) / kSortTile;
     TRY_CUDA(cudaMemsetAsync(ws->ctr, 0, kCtrCount * sizeof(uint32_t), s));
     TRY_CUDA(cudaMemsetAsync(ws->hist, 0, kSortPasses * kRadix * sizeof(uint32_t), s));
-    for (int p = 0; p < kSortPasses; ++p)
+    for (int p = 0; p < kSortPasses + ws->seg_passes; ++p)
         TRY_CUDA(cudaMemsetAsync(ws->sort_status + (size_t)p * ws->sort_tiles_max * kRadix, 0,
                                  (size_t)tiles * kRadix * sizeof(uint32_t), s));
     TRY_CUDA(cudaMemsetAsync(ws->level_status, 0, (size_t)kLevels * ws->level_tiles_max * sizeof(uint32_t), s));
@@ -482,6 +640,170 @@ tree_status_t tree_diagnostics(TreeWorkspace *ws, const void *x, const void *v, 
     if (n > 0 && (!x || !v || !m)) return TREE_ERR_ARG;
     PhaseScope ph(ws, TREE_PHASE_DIAG, as_stream(stream));
     TRY_CUDA(launch_diagnostics(ws, x, v, m, phi, n, out, as_stream(stream)));
+    return TREE_OK;
+}
+
+tree_status_t tree_diagnostics_segments(TreeWorkspace *ws, const void *x, const void *v, const void *m,
+                                        const void *phi, int64_t n, double *out, void *stream) {
+    if (!ws || !out) return TREE_ERR_ARG;
+    tree_status_t stn = check_n(ws, n);
+    if (stn != TREE_OK) return stn;
+    if (ws->nseg <= 1) return tree_diagnostics(ws, x, v, m, phi, n, out, stream);
+    if (!x || !v || !m) return TREE_ERR_ARG;
+    PhaseScope ph(ws, TREE_PHASE_DIAG, as_stream(stream));
+    TRY_CUDA(launch_diagnostics_segments(ws, x, v, m, phi, n, out, as_stream(stream)));
+    return TREE_OK;
+}
+
+tree_status_t leapfrog_graph_capture(TreeWorkspace *ws, void *x, void *v, const void *m, void *a, void *phi,
+                                     double tau, int64_t n, double *diag) {
+    if (!ws) return TREE_ERR_ARG;
+    if (!isfinite(tau)) return TREE_ERR_ARG;
+    tree_status_t st = check_n(ws, n);
+    if (st != TREE_OK) return st;
+    if (n == 0 || !x || !v || !m || !a) return TREE_ERR_ARG;
+    TRY_CUDA(cudaDeviceSynchronize());
+    drop_graph(ws);
+    if (!ws->cap_stream) TRY_CUDA(cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = ws->cap_stream;
+    // everything a step may do on the host first (the opening-criterion table)
+    st = upload_mac(ws, cs);
+    if (st != TREE_OK) return st;
+    const bool timing = ws->timing;
+    ws->timing = false;
+    const int64_t l0 = ws->launches;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        ws->timing = timing;
+        return TREE_ERR_CUDA;
+    }
+    st = leapfrog_step(ws, x, v, m, a, phi, tau, n, cs);
+    if (st == TREE_OK && diag) st = tree_diagnostics(ws, x, v, m, phi, n, diag, cs);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &g);
+    ws->timing = timing;
+    const int64_t captured = ws->launches - l0;
+    ws->launches = l0;
+    // nothing ran: the workspace holds no tree of these positions yet
+    ws->built = false;
+    ws->has_moments = false;
+    ws->list_groups = -1;
+    if (st != TREE_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st != TREE_OK ? st : TREE_ERR_CUDA;
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return TREE_ERR_CUDA;
+    }
+    ws->graph = g;
+    ws->graph_exec = ex;
+    ws->graph_launches = captured;
+    ws->graph_n = n;
+    return TREE_OK;
+}
+
+tree_status_t leapfrog_graph_launch(TreeWorkspace *ws, void *stream) {
+    if (!ws) return TREE_ERR_ARG;
+    if (!ws->graph_exec) return TREE_ERR_STATE;
+    TRY_CUDA(cudaGraphLaunch(ws->graph_exec, as_stream(stream)));
+    ws->launches += ws->graph_launches;
+    ws->n = ws->graph_n;
+    ws->built = true;
+    ws->has_moments = true;
+    ws->list_groups = -1;
+    return TREE_OK;
+}
+
+tree_status_t tree_autotune(const TreeParams *base, int64_t nseg, const int64_t *offsets, const void *x,
+                            const void *m, int64_t n, int32_t reps, TreeParams *best, double *table,
+                            int32_t *ncand, void *stream) {
+    if (!base || !best || !x || !m || n <= 0 || reps < 1) return TREE_ERR_ARG;
+    if (table && !ncand) return TREE_ERR_ARG;
+    tree_status_t st = check_params(base);
+    if (st != TREE_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    const int lcaps[3] = {4, 8, 16}, gss[3] = {16, 32, 64}, stacks[2] = {512, 1024};
+    const int32_t rows = table ? *ncand : 0;
+    int32_t used = 0;
+    double best_ms = INFINITY;
+    void *a = nullptr;
+    const size_t rs = base->precision == TREE_F64 ? 8 : 4;
+    TRY_CUDA(cudaMalloc(&a, 3 * (size_t)n * rs));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaFree(a);
+        return TREE_ERR_CUDA;
+    }
+    tree_status_t ret = TREE_OK;
+    for (int li = 0; li < 3 && ret == TREE_OK; ++li) {
+        TreeParams p = *base;
+        p.leaf_cap = lcaps[li];
+        p.node_cap = 0;
+        TreeWorkspace *ws = nullptr;
+        st = tree_workspace_create(n, &p, &ws);
+        if (st != TREE_OK) { ret = st; break; }
+        if (nseg > 1) st = tree_set_segments(ws, nseg, offsets);
+        for (int gi = 0; gi < 3 && st == TREE_OK; ++gi) {
+            for (int si = 0; si < 2 && st == TREE_OK; ++si) {
+                p.group_size = gss[gi];
+                p.stack_depth = stacks[si];
+                st = tree_set_params(ws, &p);
+                if (st != TREE_OK) break;
+                double ms = INFINITY;
+                int32_t dev = 0;
+                // one untimed evaluation, then reps timed ones
+                for (int r = 0; r <= reps && st == TREE_OK; ++r) {
+                    if (r == 1) cudaEventRecord(e0, s);
+                    st = tree_build(ws, x, n, p.precision, s);
+                    if (st == TREE_OK) st = tree_moments(ws, x, m, s);
+                    if (st == TREE_OK) st = tree_forces(ws, a, nullptr, 0, s);
+                }
+                if (st != TREE_OK) break;
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) { st = TREE_ERR_CUDA; break; }
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                st = tree_get_status(ws, &dev, 1);
+                if (st == TREE_ERR_DEVICE) st = TREE_OK;  // judged below
+                if (st != TREE_OK) break;
+                if (dev == 0) ms = (double)t / reps;  // a candidate that overflowed its stack does not count
+                if (table && used < rows) {
+                    table[4 * used + 0] = p.leaf_cap;
+                    table[4 * used + 1] = p.group_size;
+                    table[4 * used + 2] = p.stack_depth;
+                    table[4 * used + 3] = ms;
+                }
+                ++used;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    *best = p;
+                }
+            }
+        }
+        if (st != TREE_OK) ret = st;
+        tree_workspace_destroy(ws);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(a);
+    if (ncand) *ncand = used;
+    if (ret == TREE_OK && !isfinite(best_ms)) ret = TREE_ERR_DEVICE;
+    return ret;
+}
+
+tree_status_t tree_export_boxes(TreeWorkspace *ws, double *lo, int32_t *k) {
+    if (!ws || (!lo && !k)) return TREE_ERR_ARG;
+    if (!ws->built || ws->n == 0) return TREE_ERR_STATE;
+    TRY_CUDA(cudaDeviceSynchronize());
+    std::vector<DevBox> b((size_t)ws->nseg);
+    TRY_CUDA(cudaMemcpy(b.data(), ws->box, b.size() * sizeof(DevBox), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < b.size(); ++i) {
+        if (lo) for (int d = 0; d < 3; ++d) lo[3 * i + d] = b[i].lo[d];
+        if (k) k[i] = b[i].k;
+    }
     return TREE_OK;
 }
 
@@ -541,6 +863,7 @@ tree_status_t tree_get_info(TreeWorkspace *ws, TreeInfo *info) {
     info->list_pc = ws->list_groups >= 0 ? ws->list_pc : 0;
     info->list_pp = ws->list_groups >= 0 ? ws->list_pp : 0;
     info->launches = ws->launches;
+    info->n_segments = ws->nseg;
     if (!ws->built || ws->n == 0) return TREE_OK;
     uint32_t ctr[kCtrCount];
     DevBox box;
@@ -562,6 +885,7 @@ tree_status_t tree_get_info(TreeWorkspace *ws, TreeInfo *info) {
         info->pc_pairs = (int64_t)st[kStatPC];
         info->max_stack = (int64_t)st[kStatMaxStack];
     }
+    info->launches = ws->launches;  // including the statistics reduction above
     return TREE_OK;
 }
 

@@ -59,15 +59,7 @@ __global__ void __launch_bounds__(256) k_box_partial(const Real *__restrict__ x,
 // lo = min, ext = max_d (hi_d - lo_d) in FP64, L = 2^k the smallest power of
 // two strictly greater than ext (k = 0 when ext = 0): with ext = f 2^e,
 // f in [0.5, 1), that power is 2^e.
-__global__ void k_box_final(const double *__restrict__ part, int nblocks, DevBox *box) {
-    if (threadIdx.x != 0) return;
-    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
-    for (int b = 0; b < nblocks; ++b) {
-        for (int d = 0; d < 3; ++d) {
-            lo[d] = fmin(lo[d], part[b * 8 + d]);
-            hi[d] = fmax(hi[d], part[b * 8 + 3 + d]);
-        }
-    }
+__device__ void box_from_minmax(double (&lo)[3], double (&hi)[3], DevBox *box) {
     double ext = 0.0;
     for (int d = 0; d < 3; ++d) {
         if (!(lo[d] <= hi[d])) { lo[d] = 0.0; hi[d] = 0.0; }  // no finite value on this axis
@@ -82,10 +74,117 @@ __global__ void k_box_final(const double *__restrict__ part, int nblocks, DevBox
     box->unit = ldexp(1.0, k - kBits);
 }
 
+__global__ void k_box_final(const double *__restrict__ part, int nblocks, DevBox *box) {
+    if (threadIdx.x != 0) return;
+    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int b = 0; b < nblocks; ++b) {
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = fmin(lo[d], part[b * 8 + d]);
+            hi[d] = fmax(hi[d], part[b * 8 + 3 + d]);
+        }
+    }
+    box_from_minmax(lo, hi, box);
+}
+
 cudaError_t launch_box_final(TreeWorkspace *ws, int nblocks, cudaStream_t s) {
     k_box_final<<<1, 32, 0, s>>>(ws->part, nblocks, ws->box);
     ws->launches += 1;
     return cudaGetLastError();
+}
+
+// Segmented box: one block per chunk {begin, end, segment} (chunks never
+// straddle segments), optionally fused with the kick + drift of Eqs. 2-3
+// (the same arithmetic as the unsegmented kick-drift pass); then one thread
+// per segment folds its chunks.
+template <typename Real, bool KICK>
+__global__ void __launch_bounds__(256) k_box_chunks(Real *__restrict__ x, Real *__restrict__ v,
+                                                    const Real *__restrict__ a, Real half_tau, Real tau, int64_t n,
+                                                    const uint4 *__restrict__ chunks, int64_t nchunks,
+                                                    double *__restrict__ part, int32_t *dstatus) {
+    __shared__ double sh[6][8];
+    const Real big = sizeof(Real) == 4 ? (Real)FLT_MAX : (Real)DBL_MAX;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const uint4 ch = chunks[c];
+        Real mn[3] = {big, big, big}, mx[3] = {-big, -big, -big};
+        bool bad = false;
+        for (int64_t i = ch.x + threadIdx.x; i < (int64_t)ch.y; i += blockDim.x) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                Real xx;
+                if (KICK) {
+                    const Real vv = fma(half_tau, a[d * n + i], v[d * n + i]);
+                    xx = fma(tau, vv, x[d * n + i]);
+                    v[d * n + i] = vv;
+                    x[d * n + i] = xx;
+                } else {
+                    xx = x[d * n + i];
+                }
+                if (!isfinite(xx)) { bad = true; continue; }
+                mn[d] = min(mn[d], xx);
+                mx[d] = max(mx[d], xx);
+            }
+        }
+        if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(dstatus, TREE_DEV_NONFINITE);
+        double dmn[3], dmx[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            dmn[d] = mn[d] == big ? DBL_MAX : (double)mn[d];
+            dmx[d] = mx[d] == -big ? -DBL_MAX : (double)mx[d];
+            for (int o = 16; o > 0; o >>= 1) {
+                dmn[d] = fmin(dmn[d], __shfl_xor_sync(0xffffffffu, dmn[d], o));
+                dmx[d] = fmax(dmx[d], __shfl_xor_sync(0xffffffffu, dmx[d], o));
+            }
+        }
+        if (lane == 0) {
+            for (int d = 0; d < 3; ++d) { sh[d][warp] = dmn[d]; sh[3 + d][warp] = dmx[d]; }
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            const int q = threadIdx.x;
+            double r = sh[q][0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = q < 3 ? fmin(r, sh[q][w]) : fmax(r, sh[q][w]);
+            part[c * 8 + q] = r;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_box_seg_final(const double *__restrict__ part, const uint32_t *__restrict__ bfirst, int64_t nseg,
+                                DevBox *box) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nseg) return;
+    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (uint32_t c = bfirst[b]; c < bfirst[b + 1]; ++c) {
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = fmin(lo[d], part[c * 8 + d]);
+            hi[d] = fmax(hi[d], part[c * 8 + 3 + d]);
+        }
+    }
+    box_from_minmax(lo, hi, box + b);
+}
+
+template <typename Real>
+static cudaError_t box_seg_impl(TreeWorkspace *ws, Real *x, Real *v, const Real *a, double tau, int64_t n,
+                                bool kick, cudaStream_t s) {
+    const int nb = grid_for(ws->seg_nbchunk * 256, 256, 152 * 16);
+    if (kick)
+        k_box_chunks<Real, true><<<nb, 256, 0, s>>>(x, v, a, (Real)(0.5 * tau), (Real)tau, n, ws->seg_bchunk,
+                                                   ws->seg_nbchunk, ws->seg_part, ws->dstatus);
+    else
+        k_box_chunks<Real, false><<<nb, 256, 0, s>>>(x, nullptr, nullptr, Real(0), Real(0), n, ws->seg_bchunk,
+                                                    ws->seg_nbchunk, ws->seg_part, ws->dstatus);
+    k_box_seg_final<<<grid_for(ws->nseg, 128, 1 << 20), 128, 0, s>>>(ws->seg_part, ws->seg_bfirst, ws->nseg,
+                                                                     ws->box);
+    ws->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_box_segments(TreeWorkspace *ws, void *x, void *v, const void *a, double tau, int64_t n,
+                                bool kick, cudaStream_t s) {
+    if (ws->p.precision == TREE_F64)
+        return box_seg_impl<double>(ws, (double *)x, (double *)v, (const double *)a, tau, n, kick, s);
+    return box_seg_impl<float>(ws, (float *)x, (float *)v, (const float *)a, tau, n, kick, s);
 }
 
 template <typename Real>
@@ -97,6 +196,7 @@ static cudaError_t box_impl(TreeWorkspace *ws, const Real *x, int64_t n, cudaStr
 }
 
 cudaError_t launch_box(TreeWorkspace *ws, const void *x, int64_t n, cudaStream_t s) {
+    if (ws->nseg > 1) return launch_box_segments(ws, const_cast<void *>(x), nullptr, nullptr, 0.0, n, false, s);
     if (ws->p.precision == TREE_F64) return box_impl(ws, (const double *)x, n, s);
     return box_impl(ws, (const float *)x, n, s);
 }
@@ -106,10 +206,12 @@ cudaError_t launch_box(TreeWorkspace *ws, const void *x, int64_t n, cudaStream_t
 // only rounding (the scaling is by a power of two).  The key interleaves
 // q_x, q_y, q_z (x highest).  The same pass counts the eight 8-bit digits of
 // every key for the radix sort (warp-aggregated shared-memory atomics).
-template <typename Real>
+// SEG: every particle is quantised in the box of its own segment.
+template <typename Real, bool SEG>
 __global__ void __launch_bounds__(256) k_keys(const Real *__restrict__ x, int64_t n,
-                                              const DevBox *__restrict__ box,
-                                              uint64_t *__restrict__ key, uint32_t *__restrict__ hist) {
+                                              const DevBox *__restrict__ box, const int64_t *__restrict__ seg_off,
+                                              int64_t nseg, uint64_t *__restrict__ key,
+                                              uint32_t *__restrict__ hist) {
     __shared__ uint32_t sh[kSortPasses][kRadix];
     for (int i = threadIdx.x; i < kSortPasses * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
     __syncthreads();
@@ -123,11 +225,17 @@ __global__ void __launch_bounds__(256) k_keys(const Real *__restrict__ x, int64_
         uint64_t k = 0;
         if (valid) {
             double lo[3] = {lo0, lo1, lo2};
+            double sc = scale;
+            if (SEG) {
+                const DevBox *bx = box + seg_find(seg_off, nseg, i);
+                lo[0] = bx->lo[0]; lo[1] = bx->lo[1]; lo[2] = bx->lo[2];
+                sc = bx->scale;
+            }
             uint32_t q[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 double diff = __dsub_rn((double)x[d * n + i], lo[d]);
-                double f = floor(__dmul_rn(diff, scale));
+                double f = floor(__dmul_rn(diff, sc));
                 if (!(f >= 0.0)) f = 0.0;  // also catches NaN
                 if (f > qmax) f = qmax;
                 q[d] = (uint32_t)f;
@@ -174,11 +282,23 @@ struct SortSmem {
     uint32_t tile;
 };
 
-template <bool FIRST>
+// MODE: kPassFirst (values = input positions), kPassKey, kPassSeg (digit of
+// the segment index of the value's input position: segments are the most
+// significant sort digits, so each ends up in its own contiguous range).
+enum SortPass { kPassFirst = 0, kPassKey = 1, kPassSeg = 2 };
+
+template <int MODE>
+__device__ __forceinline__ uint32_t sort_digit(uint64_t k, uint32_t v, int shift, const int64_t *seg_off,
+                                               int64_t nseg) {
+    if (MODE == kPassSeg) return (seg_find(seg_off, nseg, v) >> shift) & 0xffu;
+    return (uint32_t)((k >> shift) & 0xffu);
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t n, int shift, const uint32_t *__restrict__ digit_off,
-    uint32_t *status, uint32_t *ticket, int32_t *dstatus) {
+    uint32_t *status, uint32_t *ticket, int32_t *dstatus, const int64_t *__restrict__ seg_off, int64_t nseg) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem &S = *reinterpret_cast<SortSmem *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -196,8 +316,8 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
         const int64_t pos = wbase + i * 32 + lane;
         if (pos < n) {
             k[i] = kin[pos];
-            v[i] = FIRST ? (uint32_t)pos : vin[pos];
-            dg[i] = (uint32_t)((k[i] >> shift) & 0xffu);
+            v[i] = MODE == kPassFirst ? (uint32_t)pos : vin[pos];
+            dg[i] = sort_digit<MODE>(k[i], v[i], shift, seg_off, nseg);
         } else {
             k[i] = 0; v[i] = 0; dg[i] = 0x100u;
         }
@@ -275,17 +395,26 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const int valid = rem < kSortTile ? (int)rem : kSortTile;
     for (int j = tid; j < valid; j += kSortThreads) {
         const uint64_t kk = S.keys[j];
-        const uint32_t d = (uint32_t)((kk >> shift) & 0xffu);
+        const uint32_t vv = S.vals[j];
+        const uint32_t d = sort_digit<MODE>(kk, vv, shift, seg_off, nseg);
         const uint32_t o = S.gbase[d] + (uint32_t)j - S.start[d];
         kout[o] = kk;
-        vout[o] = S.vals[j];
+        vout[o] = vv;
     }
 }
+
+// The passes alternate between the two key/value buffers and must end in
+// ws->key / ws->idx: with an odd number of passes the keys start in key_alt.
+static bool sort_starts_alt(const TreeWorkspace *ws) { return ((kSortPasses + ws->seg_passes) & 1) != 0; }
 
 template <typename Real>
 static cudaError_t keys_impl(TreeWorkspace *ws, const Real *x, int64_t n, cudaStream_t s) {
     int nb = grid_for(n, 256, 152 * 8);
-    k_keys<Real><<<nb, 256, 0, s>>>(x, n, ws->box, ws->key, ws->hist);
+    uint64_t *dst = sort_starts_alt(ws) ? ws->key_alt : ws->key;
+    if (ws->nseg > 1)
+        k_keys<Real, true><<<nb, 256, 0, s>>>(x, n, ws->box, ws->seg_off, ws->nseg, dst, ws->hist);
+    else
+        k_keys<Real, false><<<nb, 256, 0, s>>>(x, n, ws->box, nullptr, 1, dst, ws->hist);
     k_hist_scan<<<kSortPasses, kRadix, 0, s>>>(ws->hist);
     ws->launches += 2;
     return cudaGetLastError();
@@ -299,43 +428,67 @@ cudaError_t launch_keys(TreeWorkspace *ws, const void *x, int64_t n, cudaStream_
 cudaError_t launch_sort(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
     const int64_t tiles = (n + kSortTile - 1) / kSortTile;
     const size_t smem = sizeof(SortSmem);
-    cudaError_t e = cudaFuncSetAttribute(k_onesweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_onesweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    uint64_t *kin = ws->key, *kout = ws->key_alt;
-    uint32_t *vin = ws->idx, *vout = ws->idx_alt;
-    for (int p = 0; p < kSortPasses; ++p) {
+    static bool attr_done[64] = {};
+    if (ws->device < 64 && !attr_done[ws->device]) {
+        cudaError_t e = cudaFuncSetAttribute(k_onesweep<kPassFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_onesweep<kPassKey>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_onesweep<kPassSeg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done[ws->device] = true;
+    }
+    const bool alt = sort_starts_alt(ws);
+    uint64_t *kin = alt ? ws->key_alt : ws->key, *kout = alt ? ws->key : ws->key_alt;
+    uint32_t *vin = alt ? ws->idx_alt : ws->idx, *vout = alt ? ws->idx : ws->idx_alt;
+    const int npass = kSortPasses + ws->seg_passes;
+    for (int p = 0; p < npass; ++p) {
         uint32_t *st = ws->sort_status + (size_t)p * ws->sort_tiles_max * kRadix;
-        const uint32_t *off = ws->hist + kSortPasses * kRadix + p * kRadix;
         uint32_t *tk = ws->ctr + kCtrSortTicket + p;
-        if (p == 0)
-            k_onesweep<true><<<(unsigned)tiles, kSortThreads, smem, s>>>(kin, vin, kout, vout, n, 8 * p, off, st, tk, ws->dstatus);
-        else
-            k_onesweep<false><<<(unsigned)tiles, kSortThreads, smem, s>>>(kin, vin, kout, vout, n, 8 * p, off, st, tk, ws->dstatus);
+        const unsigned g = (unsigned)tiles;
+        if (p == 0) {
+            k_onesweep<kPassFirst><<<g, kSortThreads, smem, s>>>(kin, vin, kout, vout, n, 0,
+                                                                 ws->hist + kSortPasses * kRadix, st, tk,
+                                                                 ws->dstatus, nullptr, 1);
+        } else if (p < kSortPasses) {
+            k_onesweep<kPassKey><<<g, kSortThreads, smem, s>>>(kin, vin, kout, vout, n, 8 * p,
+                                                               ws->hist + kSortPasses * kRadix + p * kRadix, st, tk,
+                                                               ws->dstatus, nullptr, 1);
+        } else {
+            const int q = p - kSortPasses;
+            k_onesweep<kPassSeg><<<g, kSortThreads, smem, s>>>(kin, vin, kout, vout, n, 8 * q,
+                                                               ws->seg_digit_off + q * kRadix, st, tk, ws->dstatus,
+                                                               ws->seg_off, ws->nseg);
+        }
         uint64_t *tk_ = kin; kin = kout; kout = tk_;
         uint32_t *tv_ = vin; vin = vout; vout = tv_;
     }
-    ws->launches += kSortPasses;
-    // 8 passes: the sorted data is back in ws->key / ws->idx
+    ws->launches += npass;
+    // the sorted data is now in ws->key / ws->idx
     return cudaGetLastError();
 }
 
 // ============================================================== octree
-__global__ void k_tree_init(uint32_t *ctr, uint32_t *nfirst, uint32_t *ncount, uint32_t *nparent, int64_t n) {
+// Level 0 holds one root per segment (segment b = node b, the sorted range
+// [off[b], off[b+1])), or the single root of all n particles.
+__global__ void k_tree_init(uint32_t *ctr, uint32_t *nfirst, uint32_t *ncount, uint32_t *nparent, int64_t n,
+                            const int64_t *__restrict__ seg_off, int64_t nseg) {
     const int t = threadIdx.x;
-    if (t < kLevels + 1) {
-        ctr[kCtrLevelTrunc + t] = 0xffffffffu;
-        ctr[kCtrLevelRawEnd + t] = 0;
-        ctr[kCtrLevelStart + t] = 0;
+    if (blockIdx.x == 0) {
+        if (t < kLevels + 1) {
+            ctr[kCtrLevelTrunc + t] = 0xffffffffu;
+            ctr[kCtrLevelRawEnd + t] = 0;
+            ctr[kCtrLevelStart + t] = 0;
+        }
+        __syncthreads();
+        if (t == 0) ctr[kCtrLevelRawEnd + 0] = n > 0 ? (uint32_t)nseg : 0u;
     }
-    __syncthreads();
-    if (t == 0) {
-        ctr[kCtrLevelStart + 0] = 0;
-        ctr[kCtrLevelRawEnd + 0] = n > 0 ? 1u : 0u;
-        nfirst[0] = 0;
-        ncount[0] = (uint32_t)n;
-        nparent[0] = 0;
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + t;
+    if (b < nseg) {
+        nfirst[b] = nseg > 1 ? (uint32_t)seg_off[b] : 0u;
+        ncount[b] = nseg > 1 ? (uint32_t)(seg_off[b + 1] - seg_off[b]) : (uint32_t)n;
+        nparent[b] = (uint32_t)b;
     }
 }
 
@@ -437,8 +590,9 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(
 }
 
 cudaError_t launch_octree(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
-    k_tree_init<<<1, 32, 0, s>>>(ws->ctr, ws->nfirst, ws->ncount, ws->nparent, n);
-    double maxl = 1.0;
+    k_tree_init<<<grid_for(ws->nseg, 128, 1 << 20), 128, 0, s>>>(ws->ctr, ws->nfirst, ws->ncount, ws->nparent, n,
+                                                                 ws->seg_off, ws->nseg);
+    double maxl = (double)ws->nseg;
     for (int L = 0; L < kLevels; ++L) {
         double bound = fmin(fmin(maxl, (double)n), (double)ws->node_cap);
         int nb = grid_for((int64_t)bound, kLevelThreads, 152 * 8);

@@ -17,6 +17,9 @@ constexpr int kSortThreads = 256;  // onesweep block
 constexpr int kSortItems = 16;     // keys per thread
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSortPasses = 8;     // 8-bit digits over the 64-bit key
+constexpr int kSegPassesMax = 2;   // extra passes over the segment index (ensembles)
+constexpr int kMaxSegments = 65536;
+constexpr int kBoxChunk = 8192;    // particles per partial box of a segmented reduction
 constexpr int kRadix = 256;
 constexpr int kLevelThreads = 256;  // octree level block (nodes per tile)
 constexpr int kMaxBlocksReduce = 1024;  // partial-result slots of the reductions
@@ -55,8 +58,8 @@ struct DevBox {
 // total of level l-1, trunc the first child slot of a parent that was turned
 // into a leaf because the node array was full.
 enum CounterSlots {
-    kCtrSortTicket = 0,                       // 8 tickets
-    kCtrLevelTicket = kCtrSortTicket + 8,     // 22 tickets
+    kCtrSortTicket = 0,                       // 8 + 2 tickets
+    kCtrLevelTicket = kCtrSortTicket + 16,    // 22 tickets
     kCtrLevelStart = kCtrLevelTicket + 24,    // 23 level starts
     kCtrLevelRawEnd = kCtrLevelStart + 24,    // 23 raw ends
     kCtrLevelTrunc = kCtrLevelRawEnd + 24,    // 23 truncation points
@@ -86,12 +89,32 @@ struct TreeWorkspace {
     uint64_t *key = nullptr, *key_alt = nullptr;
     uint32_t *idx = nullptr, *idx_alt = nullptr;
     uint32_t *hist = nullptr;          // [8][256] counts, then exclusive offsets
-    uint32_t *sort_status = nullptr;   // [8][tiles][256]
+    uint32_t *sort_status = nullptr;   // [8 + 2][tiles][256]
     uint32_t *level_status = nullptr;  // [22][level_tiles]
     uint32_t *ctr = nullptr;           // kCtrCount words
     // box
     double *part = nullptr;            // reduction partials [kMaxBlocksReduce][8]
-    treegb::DevBox *box = nullptr;
+    treegb::DevBox *box = nullptr;     // one per segment
+    // segments (independent systems sharing one build; nseg = 1: a single system of any n)
+    int64_t nseg = 1;
+    std::vector<int64_t> seg_off_h;    // host copy of the offsets (nseg + 1), empty when nseg = 1
+    int64_t *seg_off = nullptr;        // device offsets [nseg + 1]
+    uint32_t *seg_cstart = nullptr;    // first Gs chunk of each segment [nseg + 1] (for the current Gs)
+    int32_t seg_cstart_gs = 0;         // Gs the chunk table was made for
+    int64_t seg_nchunks = 0;           // total Gs chunks over all segments
+    uint4 *seg_bchunk = nullptr;       // box chunks {begin, end, segment, 0}
+    uint32_t *seg_bfirst = nullptr;    // first box chunk of each segment [nseg + 1]
+    int64_t seg_nbchunk = 0;
+    double *seg_part = nullptr;        // [box chunks][8] partial min/max
+    uint32_t *seg_digit_off = nullptr; // [2][256] exclusive offsets of the segment-index digits
+    int seg_passes = 0;                // sort passes over the segment index (0, 1 or 2)
+    int64_t chunks_cap = 0;            // capacity of ccount / coff
+    int64_t box_cap = 1;               // DevBox entries allocated
+    // one captured leapfrog step (leapfrog_graph_capture)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_launches = 0, graph_n = 0;
     // sorted particles (float4 / double4a)
     void *spos = nullptr;
     // nodes
@@ -252,6 +275,18 @@ __device__ inline uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_tot, 
     return r;
 }
 
+// Segment holding sorted or input position i: the largest b < nseg with
+// off[b] <= i (off ascending, off[0] = 0).
+__device__ __forceinline__ uint32_t seg_find(const int64_t *__restrict__ off, int64_t nseg, int64_t i) {
+    uint32_t lo = 0, hi = (uint32_t)nseg - 1u;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1u) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid - 1u;
+    }
+    return lo;
+}
+
 inline int grid_for(int64_t n, int threads, int max_blocks) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -266,6 +301,8 @@ namespace treegb {
 // build.cu
 cudaError_t launch_box(TreeWorkspace *ws, const void *x, int64_t n, cudaStream_t s);
 cudaError_t launch_box_final(TreeWorkspace *ws, int nblocks, cudaStream_t s);
+cudaError_t launch_box_segments(TreeWorkspace *ws, void *x, void *v, const void *a, double tau, int64_t n,
+                                bool kick, cudaStream_t s);
 cudaError_t launch_keys(TreeWorkspace *ws, const void *x, int64_t n, cudaStream_t s);
 cudaError_t launch_sort(TreeWorkspace *ws, int64_t n, cudaStream_t s);
 cudaError_t launch_octree(TreeWorkspace *ws, int64_t n, cudaStream_t s);
@@ -296,6 +333,8 @@ cudaError_t launch_kick_drift_box(TreeWorkspace *ws, void *x, void *v, const voi
                                   int64_t n, cudaStream_t s);
 cudaError_t launch_diagnostics(TreeWorkspace *ws, const void *x, const void *v, const void *m,
                                const void *phi, int64_t n, double *out, cudaStream_t s);
+cudaError_t launch_diagnostics_segments(TreeWorkspace *ws, const void *x, const void *v, const void *m,
+                                        const void *phi, int64_t n, double *out, cudaStream_t s);
 cudaError_t launch_direct(TreeWorkspace *ws, const void *x, const void *m, int64_t n, int dtype,
                           const int64_t *targets, int64_t nt, double *a_out, double *phi_out,
                           cudaStream_t s);

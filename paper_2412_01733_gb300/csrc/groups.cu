@@ -57,6 +57,18 @@ __device__ __forceinline__ bool group_starts(const uint64_t *__restrict__ skey, 
     return ncount[node] > cmax;
 }
 
+// Chunks restart at every segment: segment b owns chunks [cstart[b],
+// cstart[b+1]), chunk c of it covering [off[b] + (c - cstart[b]) Gs, ...).
+__device__ __forceinline__ uint32_t chunk_seg(const uint32_t *__restrict__ cstart, int64_t nseg, int64_t c) {
+    uint32_t lo = 0, hi = (uint32_t)nseg - 1u;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1u) >> 1;
+        if ((int64_t)cstart[mid] <= c) lo = mid;
+        else hi = mid - 1u;
+    }
+    return lo;
+}
+
 // One warp per chunk: number of groups that start inside it.
 template <bool WRITE>
 __global__ void __launch_bounds__(256) k_group_chunks(const uint64_t *__restrict__ skey, const uint8_t *__restrict__ plev,
@@ -64,13 +76,19 @@ __global__ void __launch_bounds__(256) k_group_chunks(const uint64_t *__restrict
                                                       const uint32_t *__restrict__ nparent,
                                                       const uint32_t *__restrict__ ncount, uint32_t cmax,
                                                       int64_t n, int gs, int delta, int64_t nchunks,
+                                                      const int64_t *__restrict__ seg_off,
+                                                      const uint32_t *__restrict__ cstart, int64_t nseg,
                                                       uint32_t *__restrict__ ccount, const uint32_t *__restrict__ coff,
                                                       uint32_t *__restrict__ gfirst, const uint32_t *__restrict__ ctr) {
     const int lane = threadIdx.x & 31;
     const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (c >= nchunks) return;
-    const int64_t s0 = c * gs;
-    const int64_t s1 = min(n, s0 + gs);
+    int64_t s0 = c * gs, s1 = min(n, s0 + gs);
+    if (nseg > 1) {
+        const uint32_t b = chunk_seg(cstart, nseg, c);
+        s0 = seg_off[b] + (c - (int64_t)cstart[b]) * gs;
+        s1 = min(seg_off[b + 1], s0 + gs);
+    }
     uint32_t base = WRITE ? coff[c] : 0u;
     uint32_t total = 0;
     for (int64_t off = 0; off < gs; off += 32) {
@@ -116,7 +134,7 @@ __global__ void __launch_bounds__(kGScanThreads) k_group_scan(const uint32_t *__
 
 cudaError_t launch_groups(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
     const int gs = ws->p.group_size;
-    const int64_t nchunks = (n + gs - 1) / gs;
+    const int64_t nchunks = ws->nseg > 1 ? ws->seg_nchunks : (n + gs - 1) / gs;
     const int64_t tiles = (nchunks + kGScanTile - 1) / kGScanTile;
     cudaError_t e = cudaMemsetAsync(ws->gscan_status, 0, (size_t)tiles * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
@@ -125,11 +143,13 @@ cudaError_t launch_groups(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
     const unsigned wb = (unsigned)((nchunks * 32 + 255) / 256);
     const uint32_t cmax = 128u * (uint32_t)gs;
     k_group_chunks<false><<<wb, 256, 0, s>>>(ws->key, ws->plev, ws->pleaf, ws->nparent, ws->ncount, cmax, n, gs,
-                                            ws->p.group_split, nchunks, ws->ccount, nullptr, nullptr, ws->ctr);
+                                            ws->p.group_split, nchunks, ws->seg_off, ws->seg_cstart, ws->nseg, ws->ccount,
+                                            nullptr, nullptr, ws->ctr);
     k_group_scan<<<(unsigned)tiles, kGScanThreads, 0, s>>>(ws->ccount, ws->coff, nchunks, ws->gscan_status, ws->ctr,
                                                           ws->dstatus);
     k_group_chunks<true><<<wb, 256, 0, s>>>(ws->key, ws->plev, ws->pleaf, ws->nparent, ws->ncount, cmax, n, gs,
-                                           ws->p.group_split, nchunks, nullptr, ws->coff, ws->gfirst, ws->ctr);
+                                           ws->p.group_split, nchunks, ws->seg_off, ws->seg_cstart, ws->nseg, nullptr,
+                                           ws->coff, ws->gfirst, ws->ctr);
     ws->launches += 4;
     return cudaGetLastError();
 }

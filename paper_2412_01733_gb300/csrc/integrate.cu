@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(256) k_kick_drift_box(Real *__restrict__ x, Re
 
 cudaError_t launch_kick_drift_box(TreeWorkspace *ws, void *x, void *v, const void *a, double tau,
                                   int64_t n, cudaStream_t s) {
+    if (ws->nseg > 1) return launch_box_segments(ws, x, v, a, tau, n, true, s);
     int nb = grid_for(n, 256, kMaxBlocksReduce);
     if (ws->p.precision == TREE_F64)
         k_kick_drift_box<double><<<nb, 256, 0, s>>>((double *)x, (double *)v, (const double *)a, 0.5 * tau,
@@ -138,6 +139,82 @@ cudaError_t launch_diagnostics(TreeWorkspace *ws, const void *x, const void *v, 
         k_diag_partial<float><<<nb, 256, 0, s>>>((const float *)x, (const float *)v, (const float *)m,
                                                  (const float *)phi, n, ws->part);
     k_diag_final<<<1, 32, 0, s>>>(ws->part, nb, out);
+    ws->launches += 2;
+    return cudaGetLastError();
+}
+
+// Per-segment diagnostics: the same sums over each segment's own particles,
+// one block per box chunk (chunks never straddle segments), then one thread
+// per segment adds its chunks in order.  out: [nseg][8].
+template <typename Real>
+__global__ void __launch_bounds__(256) k_diag_chunks(const Real *__restrict__ x, const Real *__restrict__ v,
+                                                     const Real *__restrict__ m, const Real *__restrict__ phi,
+                                                     int64_t n, const uint4 *__restrict__ chunks, int64_t nchunks,
+                                                     double *__restrict__ part) {
+    __shared__ double sh[8][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const uint4 c = chunks[ch];
+        double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        Real r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int run = 0;
+        for (int64_t i = c.x + threadIdx.x; i < (int64_t)c.y; i += blockDim.x) {
+            const Real mi = m[i];
+            const Real x0 = x[i], x1 = x[n + i], x2 = x[2 * n + i];
+            const Real v0 = v[i], v1 = v[n + i], v2 = v[2 * n + i];
+            r[0] += mi * (v0 * v0 + v1 * v1 + v2 * v2);
+            if (phi) r[1] += mi * phi[i];
+            r[2] += mi * v0; r[3] += mi * v1; r[4] += mi * v2;
+            r[5] += mi * (x1 * v2 - x2 * v1);
+            r[6] += mi * (x2 * v0 - x0 * v2);
+            r[7] += mi * (x0 * v1 - x1 * v0);
+            if (++run == 32) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) { q[k] += (double)r[k]; r[k] = 0; }
+                run = 0;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) q[k] += (double)r[k];
+        q[0] *= 0.5;
+        q[1] *= 0.5;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            for (int o = 16; o > 0; o >>= 1) q[k] += __shfl_xor_sync(0xffffffffu, q[k], o);
+        if (lane == 0)
+            for (int k = 0; k < 8; ++k) sh[k][warp] = q[k];
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            double t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[threadIdx.x][w];
+            part[ch * 8 + threadIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_diag_seg_final(const double *__restrict__ part, const uint32_t *__restrict__ bfirst, int64_t nseg,
+                                 double *__restrict__ out) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nseg) return;
+    double r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t c = bfirst[b]; c < bfirst[b + 1]; ++c)
+        for (int k = 0; k < 8; ++k) r[k] += part[c * 8 + k];
+    for (int k = 0; k < 8; ++k) out[b * 8 + k] = r[k];
+}
+
+cudaError_t launch_diagnostics_segments(TreeWorkspace *ws, const void *x, const void *v, const void *m,
+                                        const void *phi, int64_t n, double *out, cudaStream_t s) {
+    const int nb = grid_for(ws->seg_nbchunk * 256, 256, 152 * 16);
+    if (ws->p.precision == TREE_F64)
+        k_diag_chunks<double><<<nb, 256, 0, s>>>((const double *)x, (const double *)v, (const double *)m,
+                                                 (const double *)phi, n, ws->seg_bchunk, ws->seg_nbchunk,
+                                                 ws->seg_part);
+    else
+        k_diag_chunks<float><<<nb, 256, 0, s>>>((const float *)x, (const float *)v, (const float *)m,
+                                                (const float *)phi, n, ws->seg_bchunk, ws->seg_nbchunk,
+                                                ws->seg_part);
+    k_diag_seg_final<<<grid_for(ws->nseg, 128, 1 << 20), 128, 0, s>>>(ws->seg_part, ws->seg_bfirst, ws->nseg, out);
     ws->launches += 2;
     return cudaGetLastError();
 }

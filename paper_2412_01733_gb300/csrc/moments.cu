@@ -19,11 +19,11 @@ namespace treegb {
 template <typename Real>
 __global__ void __launch_bounds__(256) k_moments_level(
     int L, const uint32_t *__restrict__ ctr, const uint4 *__restrict__ ngeo, const uint2 *__restrict__ nlink,
-    const typename Vec4<Real>::T *__restrict__ spos, const DevBox *__restrict__ box, double *__restrict__ mom64,
+    const typename Vec4<Real>::T *__restrict__ spos, const DevBox *__restrict__ box,
+    const uint32_t *__restrict__ nfirst, const int64_t *__restrict__ seg_off, int64_t nseg, double *__restrict__ mom64,
     int64_t cap, typename Vec4<Real>::T *__restrict__ mom_a, typename Vec4<Real>::T *__restrict__ mom_b,
     typename Vec2<Real>::T *__restrict__ mom_c) {
     const uint32_t start = ctr[kCtrLevelStart + L], end = ctr[kCtrLevelStart + L + 1];
-    const double lo0 = box->lo[0], lo1 = box->lo[1], lo2 = box->lo[2], unit = box->unit;
     double *M_ = mom64, *Rx_ = mom64 + cap, *Ry_ = mom64 + 2 * cap, *Rz_ = mom64 + 3 * cap;
     double *Q_[6];
 #pragma unroll
@@ -34,6 +34,9 @@ __global__ void __launch_bounds__(256) k_moments_level(
         const uint2 lk = nlink[node];
         const int lvl = (int)(g.w & 0xffu);
         const bool leaf = (g.w >> 8) & 1u;
+        // cell centre in the frame of the node's own segment
+        const DevBox *bx = nseg > 1 ? box + seg_find(seg_off, nseg, nfirst[node]) : box;
+        const double lo0 = bx->lo[0], lo1 = bx->lo[1], lo2 = bx->lo[2], unit = bx->unit;
         const double half = 0.5 * (double)(1u << (kBits - lvl));
         const double cx = lo0 + ((double)g.x + half) * unit;
         const double cy = lo1 + ((double)g.y + half) * unit;
@@ -103,7 +106,8 @@ static cudaError_t moments_impl(TreeWorkspace *ws, cudaStream_t s) {
     int nb = grid_for(ws->node_cap, 256, 152 * 8);
     for (int L = kMaxLevel; L >= 0; --L) {
         k_moments_level<Real><<<nb, 256, 0, s>>>(
-            L, ws->ctr, ws->ngeo, ws->nlink, (const typename Vec4<Real>::T *)ws->spos, ws->box, ws->mom64,
+            L, ws->ctr, ws->ngeo, ws->nlink, (const typename Vec4<Real>::T *)ws->spos, ws->box, ws->nfirst,
+            ws->seg_off, ws->nseg, ws->mom64,
             ws->node_cap, (typename Vec4<Real>::T *)ws->mom_a, (typename Vec4<Real>::T *)ws->mom_b,
             (typename Vec2<Real>::T *)ws->mom_c);
     }

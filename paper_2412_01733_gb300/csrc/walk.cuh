@@ -15,9 +15,11 @@
 //   (each source is a broadcast shared-memory read; the arithmetic is plain
 //   FP32 FMA plus one rsqrt per pair).  Per-tile partial sums are folded into
 //   the running sums with Kahan compensation.
-// The self pair i = j is evaluated like any other (it adds exactly 0 to the
-// acceleration) and its potential term -m_i/eps is removed at the end; with
-// eps = 0 a guarded variant skips r = 0 pairs.
+// The self pair i = j is excluded by index: a tile of near particles that
+// holds some of the group's own particles is evaluated with the mass of each
+// lane's own particle set to zero (removing -m_i/eps afterwards instead would
+// cancel in FP32 against a potential that can be far smaller than m_i/eps);
+// with eps = 0 a guarded variant also skips other r = 0 pairs.
 #pragma once
 
 #include "common.cuh"
@@ -50,6 +52,8 @@ struct WalkArgs {
     const uint32_t *order;    // processing order of the groups (widest boxes first), or NULL
     const uint32_t *gfirst;   // group g = sorted particles [gfirst[g], gfirst[g+1])
     uint32_t *ctr;            // counter block: group count and the walk's group ticket
+    const int64_t *seg_off;   // segment offsets (nseg > 1): a group walks its own segment's tree
+    int64_t nseg;
 };
 
 template <typename Real> __device__ __forceinline__ Real rsqrt_r(Real x);
@@ -68,7 +72,7 @@ __host__ __device__ constexpr size_t walk_stage_bytes() {
 // staging arrays (float4 / 32-byte double4) stay aligned.
 template <typename Real>
 __host__ __device__ constexpr size_t walk_warp_bytes(int stack_depth) {
-    return (((size_t)(stack_depth + kPPCap + kPCCap + 32) * 4 + walk_stage_bytes<Real>()) + 31) & ~(size_t)31;
+    return (((size_t)(stack_depth + kPPCap + kPCCap + 64) * 4 + walk_stage_bytes<Real>()) + 31) & ~(size_t)31;
 }
 
 // --- pair terms ------------------------------------------------------------
@@ -235,6 +239,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
     uint32_t *ppbuf = stack + SD;
     uint32_t *pcbuf = ppbuf + kPPCap;
     int *mark = reinterpret_cast<int *>(pcbuf + kPCCap);
+    uint32_t *sidx = reinterpret_cast<uint32_t *>(mark + 32);  // sorted index of each staged near source
     const uint32_t lt = lanemask_lt();
 
     const V4 *__restrict__ spos = reinterpret_cast<const V4 *>(A.spos);
@@ -296,7 +301,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
     const float2 eps2v = make_float2((float)A.eps2, (float)A.eps2);
     const float2 neg1 = make_float2(-1.f, -1.f), halfv = make_float2(0.5f, 0.5f), m25 = make_float2(-2.5f, -2.5f);
 
-    auto stage_pp = [&](const V4 &src, int ns) {
+    // true when some staged source is one of the group's own particles
+    auto stage_pp = [&](const V4 &src, uint32_t si, int ns) -> bool {
+        sidx[lane] = lane < ns ? si : 0xffffffffu;
+        const bool own = __any_sync(0xffffffffu, lane < ns && si - (uint32_t)s0 < (uint32_t)cnt);
         if constexpr (sizeof(Real) == 4) {
             const int ne = (ns + 1) & ~1;
             if (lane < ne) {
@@ -311,8 +319,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
         } else {
             if (lane < ns) stA[lane] = src;
         }
+        return own;
     };
-    auto eval_pp_stage = [&](int ns) {
+    auto eval_pp_stage = [&](int ns, bool own) {
         if constexpr (sizeof(Real) == 4) {
             float2 part[TPL][4];
 #pragma unroll
@@ -320,7 +329,20 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
 #pragma unroll
                 for (int c = 0; c < 4; ++c) part[t][c] = make_float2(0.f, 0.f);
             const int np = (ns + 1) >> 1;
-            if (np == 16) {
+            if (own) {
+                // the group's own particles are in this tile: each lane drops its own index
+                for (int k = 0; k < np; ++k) {
+                    const float4 a = stF[5 * k], b = stF[5 * k + 1];
+                    const uint32_t i0 = sidx[2 * k], i1 = sidx[2 * k + 1];
+#pragma unroll
+                    for (int t = 0; t < TPL; ++t) {
+                        const uint32_t me = (uint32_t)s0 + (uint32_t)(lane + 32 * t);
+                        const float2 mm = make_float2(i0 == me ? 0.f : b.z, i1 == me ? 0.f : b.w);
+                        pp_pair<SOFT>(nX[t], nY[t], nZ[t], make_float2(a.x, a.y), make_float2(a.z, a.w),
+                                      make_float2(b.x, b.y), mm, eps2v, neg1, part[t]);
+                    }
+                }
+            } else if (np == 16) {
 #pragma unroll 4
                 for (int k = 0; k < 16; ++k) {
                     const float4 a = stF[5 * k], b = stF[5 * k + 1];
@@ -353,8 +375,13 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
                 for (int c = 0; c < 4; ++c) part[t][c] = Real(0);
             for (int j = 0; j < ns; ++j) {
                 const V4 s = stA[j];
+                const uint32_t sj = sidx[j];
 #pragma unroll
-                for (int t = 0; t < TPL; ++t) pp_term<Real, SOFT>(px[t], py[t], pz[t], s, eps2, part[t]);
+                for (int t = 0; t < TPL; ++t) {
+                    V4 st = s;
+                    if (own && sj == (uint32_t)s0 + (uint32_t)(lane + 32 * t)) st.w = Real(0);
+                    pp_term<Real, SOFT>(px[t], py[t], pz[t], st, eps2, part[t]);
+                }
             }
 #pragma unroll
             for (int t = 0; t < TPL; ++t) fold<Real, KAHAN>(sum[t], cmp[t], part[t]);
@@ -362,20 +389,21 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
     };
     auto eval_pp_list = [&](const uint32_t *buf, int ns) {
         V4 s{};
-        if (lane < ns) s = spos[buf[lane]];
+        uint32_t si = 0xffffffffu;
+        if (lane < ns) { si = buf[lane]; s = spos[si]; }
         __syncwarp();
-        stage_pp(s, ns);
+        const bool own = stage_pp(s, si, ns);
         __syncwarp();
-        eval_pp_stage(ns);
+        eval_pp_stage(ns, own);
         __syncwarp();
     };
     auto eval_pp_range = [&](uint32_t first, int ns) {
         V4 s{};
         if (lane < ns) s = spos[first + lane];
         __syncwarp();
-        stage_pp(s, ns);
+        const bool own = stage_pp(s, first + (uint32_t)lane, ns);
         __syncwarp();
-        eval_pp_stage(ns);
+        eval_pp_stage(ns, own);
         __syncwarp();
     };
     auto eval_pc_list = [&](const uint32_t *buf, int ns) {
@@ -470,7 +498,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
     uint32_t n_pc = 0, n_pp = 0, n_ppl = 0, max_top = 1;
     int top = 1, npc = 0, npp = 0;
     // Stack entries are child ranges: first node | (count - 1) << 29.
-    if (lane == 0) stack[0] = 0u;  // the root: range (node 0, 1 node)
+    // the root of the group's segment (node b at level 0): range (node b, 1 node)
+    if (lane == 0) stack[0] = A.nseg > 1 ? seg_find(A.seg_off, A.nseg, s0) : 0u;
     __syncwarp();
     bool overflow = false;
     while (top > 0) {
@@ -614,7 +643,6 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
                 } else {
                     ax = sum[t][0]; ay = sum[t][1]; az = sum[t][2]; ph = sum[t][3];
                 }
-                if (SOFT) ph += pm[t] / (Real)A.eps;  // remove the self term -m_i / eps
                 ax *= G; ay *= G; az *= G; ph *= G;
                 Real *a = reinterpret_cast<Real *>(A.a);
                 const int64_t n = A.n;
@@ -668,6 +696,8 @@ inline WalkArgs make_walk_args(TreeWorkspace *ws, const WalkOut &out) {
     a.order = ws->gorder;
     a.gfirst = ws->gfirst;
     a.ctr = ws->ctr;
+    a.seg_off = ws->seg_off;
+    a.nseg = ws->nseg;
     return a;
 }
 

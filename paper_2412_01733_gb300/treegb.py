@@ -35,7 +35,8 @@ class TreeInfo(ctypes.Structure):
                 ("box_k", ctypes.c_int32), ("box_lo", ctypes.c_double * 3),
                 ("level_offset", ctypes.c_int64 * 23), ("pp_pairs", ctypes.c_int64),
                 ("pc_pairs", ctypes.c_int64), ("max_stack", ctypes.c_int64), ("n_groups", ctypes.c_int64),
-                ("list_pc", ctypes.c_int64), ("list_pp", ctypes.c_int64), ("launches", ctypes.c_int64)]
+                ("list_pc", ctypes.c_int64), ("list_pp", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("n_segments", ctypes.c_int64)]
 
 
 class TreeError(RuntimeError):
@@ -73,6 +74,14 @@ _SIGNATURES = {
     "tree_direct_forces_noalloc": [_vp, _vp, _i64, _i32, _dbl, _dbl, _vp, _i64, _vp, _vp, _vp],
     "tree_timing_enable": [_vp, _i32],
     "tree_timing_read": [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
+    "tree_set_segments": [_vp, _i64, ctypes.POINTER(_i64)],
+    "tree_get_segments": [_vp, ctypes.POINTER(_i64)],
+    "tree_diagnostics_segments": [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp],
+    "leapfrog_graph_capture": [_vp, _vp, _vp, _vp, _vp, _vp, _dbl, _i64, _vp],
+    "leapfrog_graph_launch": [_vp, _vp],
+    "tree_autotune": [ctypes.POINTER(TreeParams), _i64, ctypes.POINTER(_i64), _vp, _vp, _i64, _i32,
+                      ctypes.POINTER(TreeParams), ctypes.POINTER(_dbl), ctypes.POINTER(_i32), _vp],
+    "tree_export_boxes": [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i32)],
     "tree_status_string": [_i32],
     "tree_version": [],
 }
@@ -122,6 +131,34 @@ def default_params(**kw) -> TreeParams:
             v = {"f32": F32, "f64": F64}[v]
         setattr(p, k, v)
     return p
+
+
+def _offsets(offsets):
+    offs = [int(o) for o in offsets]
+    arr = (_i64 * len(offs))(*offs)
+    return len(offs) - 1, arr
+
+
+def autotune(x, m, offsets=None, reps=3, **params):
+    """Fastest (leaf_cap, group_size, stack_depth) for one force evaluation of (x, m)
+    (ensemble: offsets as in Workspace.set_segments).  Returns (TreeParams, table)
+    with table rows (leaf_cap, group_size, stack_depth, ms)."""
+    base = default_params(**params)
+    dt = torch.float64 if base.precision == F64 else torch.float32
+    n = x.shape[1]
+    if not x.is_cuda or x.dtype != dt or tuple(x.shape) != (3, n) or not x.is_contiguous():
+        raise ValueError("x must be a contiguous CUDA tensor (3, n) of the parameters' precision")
+    if not m.is_cuda or m.dtype != dt or tuple(m.shape) != (n,) or not m.is_contiguous():
+        raise ValueError("m must be a contiguous CUDA tensor (n,) of the parameters' precision")
+    nseg, arr = _offsets(offsets) if offsets is not None else (0, None)
+    best = TreeParams()
+    rows = 32
+    table = (_dbl * (4 * rows))()
+    nc = _i32(rows)
+    _check("tree_autotune", lib().tree_autotune(ctypes.byref(base), nseg, arr, _ptr(x), _ptr(m), n, int(reps),
+                                                ctypes.byref(best), table, ctypes.byref(nc), _stream()))
+    tab = [tuple(table[4 * i + k] for k in range(4)) for i in range(min(nc.value, rows))]
+    return best, tab
 
 
 def _stream():
@@ -194,6 +231,57 @@ class Workspace:
             setattr(p, k, v)
         _check("tree_set_params", lib().tree_set_params(self._h, ctypes.byref(p)))
         self.params = p
+
+    def set_segments(self, offsets=None):
+        """Independent systems: system b = particles [offsets[b], offsets[b+1]) (see
+        tree_set_segments); None returns to a single system."""
+        if offsets is None:
+            _check("tree_set_segments", lib().tree_set_segments(self._h, 0, None))
+            return
+        nseg, arr = _offsets(offsets)
+        _check("tree_set_segments", lib().tree_set_segments(self._h, nseg, arr))
+
+    def segments(self) -> int:
+        v = _i64(0)
+        _check("tree_get_segments", lib().tree_get_segments(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    def diagnostics_segments(self, x, v, m, phi=None, out=None):
+        """Per-system FP64 diagnostics, float64 CUDA tensor (nseg, 8)."""
+        n = x.shape[1]
+        self._vec(x, n, "x"); self._vec(v, n, "v"); self._scal(m, n, "m")
+        self._scal(phi, n, "phi", optional=True)
+        if out is None:
+            out = torch.empty((self.segments(), 8), dtype=torch.float64, device="cuda")
+        _check("tree_diagnostics_segments", lib().tree_diagnostics_segments(self._h, _ptr(x), _ptr(v), _ptr(m),
+                                                                            _ptr(phi), n, _ptr(out), _stream()))
+        return out
+
+    def graph_capture(self, x, v, m, a, tau, phi=None, diag=None):
+        """Capture one leapfrog step (plus diagnostics into diag, a float64 CUDA tensor of 8,
+        if given) as a CUDA graph; graph_launch() replays it on the current stream."""
+        n = x.shape[1]
+        self._vec(x, n, "x"); self._vec(v, n, "v"); self._scal(m, n, "m"); self._vec(a, n, "a")
+        self._scal(phi, n, "phi", optional=True)
+        if diag is not None and (not diag.is_cuda or diag.dtype != torch.float64 or diag.numel() < 8):
+            raise ValueError("diag must be a CUDA float64 tensor of 8")
+        _check("leapfrog_graph_capture", lib().leapfrog_graph_capture(self._h, _ptr(x), _ptr(v), _ptr(m), _ptr(a),
+                                                                      _ptr(phi), float(tau), n, _ptr(diag)))
+        self._graph_keep = (x, v, m, a, phi, diag)  # the graph holds these pointers
+        self._graph_n = n
+
+    def graph_launch(self):
+        _check("leapfrog_graph_launch", lib().leapfrog_graph_launch(self._h, _stream()))
+        self.n = self._graph_n
+
+    def export_boxes(self):
+        """Per-system box of the last build: (lo float64 (nseg, 3), k int32 (nseg,)) on the host."""
+        ns = self.segments()
+        lo = (_dbl * (3 * ns))()
+        k = (_i32 * ns)()
+        _check("tree_export_boxes", lib().tree_export_boxes(self._h, lo, k))
+        return (torch.tensor(list(lo), dtype=torch.float64).reshape(ns, 3),
+                torch.tensor(list(k), dtype=torch.int32))
 
     def build(self, x):
         n = x.shape[1]
@@ -306,7 +394,7 @@ class Workspace:
         return dict(n=i.n, n_nodes=i.n_nodes, depth=i.depth, box_k=i.box_k, box_lo=list(i.box_lo),
                     level_offset=list(i.level_offset), pp_pairs=i.pp_pairs, pc_pairs=i.pc_pairs,
                     max_stack=i.max_stack, n_groups=i.n_groups, list_pc=i.list_pc, list_pp=i.list_pp,
-                    launches=i.launches)
+                    launches=i.launches, n_segments=i.n_segments)
 
     def timing(self, enable=True):
         """Start (enable=True) or stop per-phase GPU event timing."""

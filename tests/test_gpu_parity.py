@@ -139,6 +139,25 @@ def test_fp64_parity(orc, name, kind, n, p):
     assert np.max(np.abs(_np64(phi) - ref.phi) / np.abs(ref.phi)) <= 1e-11
 
 
+def test_sparse_potential_far_below_self_term(orc):
+    """Particles far apart compared with eps: |phi_i| is below 1e-4 of m_i/eps,
+    so the self pair must be left out, not added and subtracted in FP32
+    (that would cost ~1e-3 relative)."""
+    g = torch.Generator().manual_seed(9)
+    n = 200
+    x = torch.rand((3, n), generator=g, dtype=torch.float64) * 1e5
+    m = torch.full((n,), 1.0 / n, dtype=torch.float64)
+    p = dict(eps=0.01, theta=0.7, order=2, leaf_cap=4, group_size=32)
+    ws, xg, mg, a, phi = _run(x, m, **p)
+    assert ws.status() == 0
+    ref = orc.tree_forces(_np64(xg), _np64(mg), eps=0.01, theta=0.7, lcap=4, gs=32, quad=True)
+    assert np.abs(ref.phi).max() < 1e-4 * (1.0 / n) / 0.01
+    ep = np.abs(_np64(phi) - ref.phi) / np.abs(ref.phi)
+    assert np.median(ep) <= 1e-5 and ep.max() <= 1e-4, (np.median(ep), ep.max())
+    e = _rel_err(_np64(a), ref.a)
+    assert np.median(e) <= 1e-5 and e.max() <= 1e-4
+
+
 def test_kahan_off_still_within_tolerance(orc):
     x, m = _gen("plummer", 20000)
     p = dict(eps=0.01, theta=0.6, order=2, leaf_cap=16, group_size=32)
