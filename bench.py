@@ -68,6 +68,8 @@ def _args():
                          "adjoint: gradients through 16 KDK steps of Plummer N=262144 (times, FP32 vs FP64, "
                          "tree vs theta=0, finite differences)")
     ap.add_argument("--study-steps", type=int, default=100)
+    ap.add_argument("--nvtx", action="store_true",
+                    help="mark each timed step with an NVTX range named 'step' (for profiler selection)")
     return ap.parse_args()
 
 
@@ -177,7 +179,11 @@ def run_ours(a):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(a.steps):
+        if a.nvtx:
+            torch.cuda.nvtx.range_push("step")
         step()
+        if a.nvtx:
+            torch.cuda.nvtx.range_pop()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -436,6 +442,23 @@ def study_threads(a):
             print(json.dumps({"study": "threads", "n": n, "threads": M, "host_cpus": ncpu, "T_s": T, "T_sem": dT,
                               "S": S, "S_err": dS, "E": S / M, "E_err": dS / M}), flush=True)
         O.set_threads(ncpu)
+    # efficiency against N at M = 4 threads (the paper's E(N) view), N = 2^17 .. 2^21
+    for lg in range(17, 22):
+        n = 1 << lg
+        x, _, m = inputs.galaxy(n, SEED, dtype=torch.float64)
+        x, m = x.numpy(), m.numpy()
+        T = {}
+        for M in (1, 4):
+            O.set_threads(M)
+            ts = []
+            for _ in range(2):
+                t0 = time.perf_counter()
+                O.tree_forces(x, m, eps=PARAMS["eps"], theta=1.0, lcap=PARAMS["leaf_cap"], gs=PARAMS["group_size"])
+                ts.append(time.perf_counter() - t0)
+            T[M] = min(ts)
+        print(json.dumps({"study": "threads_vs_n", "n": n, "threads": 4, "T1_s": T[1], "T4_s": T[4],
+                          "S": T[1] / T[4], "E": T[1] / T[4] / 4}), flush=True)
+    O.set_threads(ncpu)
 
 
 def study_ensemble(a):
