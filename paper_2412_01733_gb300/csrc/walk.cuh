@@ -61,21 +61,12 @@ template <> __device__ __forceinline__ float rsqrt_r<float>(float x) { return rs
 template <> __device__ __forceinline__ double rsqrt_r<double>(double x) { return rsqrt(x); }
 
 // Source staging per warp: FP32 uses 16 source pairs x 5 float4 (pair-
-// interleaved, see pp_pair / pc_pair) for near particles plus a ring of 64
-// far cells (32 pairs x 5 float4) filled by asynchronous copies during the
-// traversal; FP64 uses 32 x (double4, double4, double2).
+// interleaved, see pp_pair / pc_pair); FP64 uses 32 x (double4, double4, double2).
 template <typename Real>
 __host__ __device__ constexpr size_t walk_stage_bytes() {
-    return sizeof(Real) == 4 ? (80 + 160) * sizeof(float4)
+    return sizeof(Real) == 4 ? 80 * sizeof(float4)
                              : 32 * (sizeof(typename Vec4<Real>::T) * 2 + sizeof(typename Vec2<Real>::T));
 }
-
-// 4-byte asynchronous global -> shared copy (completes at cp_async_wait).
-__device__ __forceinline__ void cp_async4(void *dst_smem, const void *src) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst_smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Per-warp shared-memory slice, rounded up to 32 bytes so that every warp's
 // staging arrays (float4 / 32-byte double4) stay aligned.
@@ -160,10 +151,9 @@ __device__ __forceinline__ void pp_pair(float2 nx, float2 ny, float2 nz, float2 
     acc[3] = __ffma2_rn(neg1, mr, acc[3]);
 }
 
-// PC for two cells.  With u = R - r_i (= -y) and the negated quadrupole
-// Qn = -Q (the FP32 walk copies of the moments store -Q), w = Qn u equals
-// Q y, u.w = -(y.Q.y), and the terms of pc_term become
-// a = [M/r^3 - 5/2 (u.w)/r^7] u + w/r^5, phi = -M/r + 1/2 (u.w)/r^5.
+// PC for two cells.  With u = R - r_i (= -y) and the staged negated
+// quadrupole Qn = -Q, w = Qn u equals Q y, u.w = -(y.Q.y), and the terms of
+// pc_term become a = [M/r^3 - 5/2 (u.w)/r^7] u + w/r^5, phi = -M/r + 1/2 (u.w)/r^5.
 template <bool QUAD, bool SOFT>
 __device__ __forceinline__ void pc_pair(float2 nx, float2 ny, float2 nz, const float4 &A, const float4 &B,
                                         const float4 &C, const float4 &D, const float4 &E, float2 eps2,
@@ -244,8 +234,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
     V4 *stA = reinterpret_cast<V4 *>(wb);            // FP64 layout
     V4 *stB = stA + 32;
     V2 *stC = reinterpret_cast<V2 *>(stB + 32);
-    float4 *stF = reinterpret_cast<float4 *>(wb);    // FP32 pair-interleaved layout (near particles)
-    float4 *stPC = stF + 80;                          // FP32 ring of 64 far cells, pair-interleaved
+    float4 *stF = reinterpret_cast<float4 *>(wb);    // FP32 pair-interleaved layout
     uint32_t *stack = reinterpret_cast<uint32_t *>(wb + walk_stage_bytes<Real>());
     uint32_t *ppbuf = stack + SD;
     uint32_t *pcbuf = ppbuf + kPPCap;
@@ -417,69 +406,63 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
         eval_pp_stage(ns, own);
         __syncwarp();
     };
-    // FP32 far cells: lane-issued asynchronous copies into ring slot `slot`
-    // (pair slot >> 1, half slot & 1) during the traversal
-    auto pc_copy = [&](int slot, uint32_t cell) {
-        float *q = reinterpret_cast<float *>(stPC + 5 * (slot >> 1)) + (slot & 1);
-        const float *a = reinterpret_cast<const float *>(momA + cell);
-        cp_async4(q + 0, a + 0); cp_async4(q + 2, a + 1); cp_async4(q + 4, a + 2); cp_async4(q + 6, a + 3);
-        if (QUAD) {
-            const float *b = reinterpret_cast<const float *>(momB + cell);
-            const float *c = reinterpret_cast<const float *>(momC + cell);
-            cp_async4(q + 8, b + 0); cp_async4(q + 10, b + 1); cp_async4(q + 12, b + 2); cp_async4(q + 14, b + 3);
-            cp_async4(q + 16, c + 0); cp_async4(q + 18, c + 1);
-        }
-    };
-    // evaluate ring slots [head, head + ns), ns <= 32, head in {0, 32}
-    auto eval_pc_ring = [&](int head, int ns) {
-        cp_async_wait();
-        __syncwarp();
-        if ((ns & 1) && lane == 0) {
-            // odd count: the partner of the last cell is a massless source at the origin
-            float *q = reinterpret_cast<float *>(stPC + 5 * ((head + ns) >> 1)) + 1;
+    auto eval_pc_list = [&](const uint32_t *buf, int ns) {
+        if constexpr (sizeof(Real) == 4) {
+            const int ne = (ns + 1) & ~1;
+            if (lane < ne) {
+                float *q = reinterpret_cast<float *>(stF + 5 * (lane >> 1));
+                const int sl = lane & 1;
+                V4 a{};
+                V4 b{};
+                V2 c{};
+                if (lane < ns) {
+                    const uint32_t cell = buf[lane];
+                    a = momA[cell];
+                    if (QUAD) { b = momB[cell]; c = momC[cell]; }
+                }
+                q[sl] = a.x; q[2 + sl] = a.y; q[4 + sl] = a.z; q[6 + sl] = a.w;
+                if (QUAD) {
+                    q[8 + sl] = -b.x; q[10 + sl] = -b.y; q[12 + sl] = -b.z; q[14 + sl] = -b.w;
+                    q[16 + sl] = -c.x; q[18 + sl] = -c.y;
+                }
+            }
+            __syncwarp();
+            float2 part[TPL][4];
 #pragma unroll
-            for (int k = 0; k < 10; ++k) q[2 * k] = 0.f;
-        }
-        __syncwarp();
-        const float4 *ring = stPC + 5 * (head >> 1);
-        float2 part[TPL][4];
+            for (int t = 0; t < TPL; ++t)
 #pragma unroll
-        for (int t = 0; t < TPL; ++t)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) part[t][c] = make_float2(0.f, 0.f);
-        const int np = (ns + 1) >> 1;
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (np == 16) {
+                for (int c = 0; c < 4; ++c) part[t][c] = make_float2(0.f, 0.f);
+            const int np = (ns + 1) >> 1;
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (np == 16) {
 #pragma unroll 2
-            for (int k = 0; k < 16; ++k) {
-                const float4 a = ring[5 * k], b = ring[5 * k + 1];
-                const float4 c = QUAD ? ring[5 * k + 2] : z4, d = QUAD ? ring[5 * k + 3] : z4,
-                             e = QUAD ? ring[5 * k + 4] : z4;
+                for (int k = 0; k < 16; ++k) {
+                    const float4 a = stF[5 * k], b = stF[5 * k + 1];
+                    const float4 c = QUAD ? stF[5 * k + 2] : z4, d = QUAD ? stF[5 * k + 3] : z4,
+                                 e = QUAD ? stF[5 * k + 4] : z4;
 #pragma unroll
-                for (int t = 0; t < TPL; ++t)
-                    pc_pair<QUAD, SOFT>(nX[t], nY[t], nZ[t], a, b, c, d, e, eps2v, neg1, halfv, m25, part[t]);
+                    for (int t = 0; t < TPL; ++t)
+                        pc_pair<QUAD, SOFT>(nX[t], nY[t], nZ[t], a, b, c, d, e, eps2v, neg1, halfv, m25, part[t]);
+                }
+            } else {
+                for (int k = 0; k < np; ++k) {
+                    const float4 a = stF[5 * k], b = stF[5 * k + 1];
+                    const float4 c = QUAD ? stF[5 * k + 2] : z4, d = QUAD ? stF[5 * k + 3] : z4,
+                                 e = QUAD ? stF[5 * k + 4] : z4;
+#pragma unroll
+                    for (int t = 0; t < TPL; ++t)
+                        pc_pair<QUAD, SOFT>(nX[t], nY[t], nZ[t], a, b, c, d, e, eps2v, neg1, halfv, m25, part[t]);
+                }
             }
+#pragma unroll
+            for (int t = 0; t < TPL; ++t) {
+                Real p1[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) p1[c] = (Real)(part[t][c].x + part[t][c].y);
+                fold<Real, KAHAN>(sum[t], cmp[t], p1);
+            }
+            __syncwarp();
         } else {
-            for (int k = 0; k < np; ++k) {
-                const float4 a = ring[5 * k], b = ring[5 * k + 1];
-                const float4 c = QUAD ? ring[5 * k + 2] : z4, d = QUAD ? ring[5 * k + 3] : z4,
-                             e = QUAD ? ring[5 * k + 4] : z4;
-#pragma unroll
-                for (int t = 0; t < TPL; ++t)
-                    pc_pair<QUAD, SOFT>(nX[t], nY[t], nZ[t], a, b, c, d, e, eps2v, neg1, halfv, m25, part[t]);
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < TPL; ++t) {
-            Real p1[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) p1[c] = (Real)(part[t][c].x + part[t][c].y);
-            fold<Real, KAHAN>(sum[t], cmp[t], p1);
-        }
-        __syncwarp();  // the ring slots may be refilled after this
-    };
-    auto eval_pc_list = [&](const uint32_t *buf, int ns) {  // FP64: staged from the index buffer
-        {
             if (lane < ns) {
                 const uint32_t c = buf[lane];
                 stA[lane] = momA[c];
@@ -513,7 +496,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
         pp_base = A.list_off[A.ngroups + 1 + g];
     }
     uint32_t n_pc = 0, n_pp = 0, n_ppl = 0, max_top = 1;
-    int top = 1, npc = 0, npp = 0, pc_head = 0;
+    int top = 1, npc = 0, npp = 0;
     // Stack entries are child ranges: first node | (count - 1) << 29.
     // the root of the group's segment (node b at level 0): range (node b, 1 node)
     if (lane == 0) stack[0] = A.nseg > 1 ? seg_find(A.seg_off, A.nseg, s0) : 0u;
@@ -573,11 +556,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
         const uint32_t fm = __ballot_sync(0xffffffffu, far);
         const uint32_t nf = __popc(fm);
         if (MODE == kWalkForce) {
-            if constexpr (sizeof(Real) == 4) {
-                if (far) pc_copy((pc_head + npc + __popc(fm & lt)) & 63, node);
-            } else {
-                if (far) pcbuf[npc + __popc(fm & lt)] = node;
-            }
+            if (far) pcbuf[npc + __popc(fm & lt)] = node;
             npc += nf;
         } else if (MODE == kWalkEmit) {
             if (far) A.pc_list[pc_base + n_pc + __popc(fm & lt)] = (int32_t)node;
@@ -621,20 +600,13 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
                 for (uint32_t o = 0; o < c; o += 32) eval_pp_range(f + o, (int)min(32u, c - o));
             }
             if (npc >= 32) {
-                if constexpr (sizeof(Real) == 4) {
-                    // the rest (< 32) is already in the other half of the ring
-                    eval_pc_ring(pc_head, 32);
-                    pc_head ^= 32;
-                    npc -= 32;
-                } else {
-                    eval_pc_list(pcbuf, 32);
-                    const int r = npc - 32;
-                    uint32_t t = lane < r ? pcbuf[32 + lane] : 0;
-                    __syncwarp();
-                    if (lane < r) pcbuf[lane] = t;
-                    __syncwarp();
-                    npc = r;
-                }
+                eval_pc_list(pcbuf, 32);
+                const int r = npc - 32;
+                uint32_t t = lane < r ? pcbuf[32 + lane] : 0;
+                __syncwarp();
+                if (lane < r) pcbuf[lane] = t;
+                __syncwarp();
+                npc = r;
             }
             if (npp >= 32) {
                 const int ntile = npp >> 5;
@@ -651,11 +623,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
         }
     }
     if (MODE == kWalkForce) {
-        if constexpr (sizeof(Real) == 4) {
-            if (npc > 0) eval_pc_ring(pc_head, npc);
-        } else {
-            if (npc > 0) eval_pc_list(pcbuf, npc);
-        }
+        if (npc > 0) eval_pc_list(pcbuf, npc);
         if (npp > 0) eval_pp_list(ppbuf, npp);
     }
     if (overflow && lane == 0) set_status(A.dstatus, TREE_DEV_STACK);
