@@ -236,6 +236,35 @@ def run_ours(a):
         out["force_err_vs_direct"] = {"median": float(err.median()), "p99": float(err.quantile(0.99)),
                                       "max": float(err.max()), "samples": 4096,
                                       "reference": "GPU direct sum, FP32 pairs, compensated, FP64 chunk totals"}
+        # end to end through the C ABI with host-resident state
+        xh = x.cpu().pin_memory(); vh = v.cpu().pin_memory(); mh = m.cpu().pin_memory()
+        ah = acc.cpu().pin_memory(); dh = torch.empty(8, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            x.copy_(xh, non_blocking=True); v.copy_(vh, non_blocking=True)
+            m.copy_(mh, non_blocking=True); acc.copy_(ah, non_blocking=True)
+            ws.leapfrog_step(x, v, m, acc, TAU, phi=phi)
+            ws.diagnostics(x, v, m, phi, out=diag)
+            xh.copy_(x, non_blocking=True); vh.copy_(v, non_blocking=True)
+            ah.copy_(acc, non_blocking=True); dh.copy_(diag, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        clocks_e2e = Clocks(local)
+        clocks_e2e.start()
+        h0 = torch.cuda.Event(enable_timing=True); h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(a.steps):
+            e2e_step()
+        h1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ck_e2e = clocks_e2e.stop()
+        te = max_over_ranks(h0.elapsed_time(h1) / 1e3)
+        out["e2e"] = {"value": world * n * a.steps / te, "unit": UNIT,
+                      "h2d_bytes_per_step": 40 * n, "d2h_bytes_per_step": 36 * n + 64, "clocks": ck_e2e}
+        del xh, vh, mh, ah, dh
         # same-GPU FP64 plain path: one force evaluation (build + moments + walk) on the same state
         x64, m64 = x.double().contiguous(), m.double().contiguous()
         del ad
@@ -269,31 +298,6 @@ def run_ours(a):
         del ws64, x64, m64, a64, p64, a32, p32
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-        # end to end through the C ABI with host-resident state
-        xh = x.cpu().pin_memory(); vh = v.cpu().pin_memory(); mh = m.cpu().pin_memory()
-        ah = acc.cpu().pin_memory(); dh = torch.empty(8, dtype=torch.float64).pin_memory()
-
-        def e2e_step():
-            x.copy_(xh, non_blocking=True); v.copy_(vh, non_blocking=True)
-            m.copy_(mh, non_blocking=True); acc.copy_(ah, non_blocking=True)
-            ws.leapfrog_step(x, v, m, acc, TAU, phi=phi)
-            ws.diagnostics(x, v, m, phi, out=diag)
-            xh.copy_(x, non_blocking=True); vh.copy_(v, non_blocking=True)
-            ah.copy_(acc, non_blocking=True); dh.copy_(diag, non_blocking=True)
-
-        e2e_step()
-        torch.cuda.synchronize()
-        barrier()
-        h0 = torch.cuda.Event(enable_timing=True); h1 = torch.cuda.Event(enable_timing=True)
-        h0.record(stream)
-        for _ in range(a.steps):
-            e2e_step()
-        h1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        te = max_over_ranks(h0.elapsed_time(h1) / 1e3)
-        out["e2e"] = {"value": world * n * a.steps / te, "unit": UNIT,
-                      "h2d_bytes_per_step": 40 * n, "d2h_bytes_per_step": 36 * n + 64}
         # the FP64 CPU oracle on the host cores, bounded sample, rank 0 at N = 1 only
         if world == 1:
             out["cpu_baseline"] = cpu_baseline(a.cpu_sample)
@@ -556,10 +560,15 @@ def study_adjoint(a):
         xK, vK, WK = TreeLeapfrog.apply(x, v, m, ws, K, tau, ck)
         loss = (xK[:, :nsel].double() ** 2).sum() + WK
         e[1].record()
+        torch.cuda.synchronize()
+        ws.timing(True)
         loss.backward()
         e[2].record(); torch.cuda.synchronize()
+        phases, _ = ws.timing_read()
+        ws.timing(False)
         st = ws.status()
-        out = dict(loss=float(loss), fwd_ms=e[0].elapsed_time(e[1]), bwd_ms=e[1].elapsed_time(e[2]), status=st)
+        out = dict(loss=float(loss), fwd_ms=e[0].elapsed_time(e[1]), bwd_ms=e[1].elapsed_time(e[2]), status=st,
+                   bwd_phase_ms={k: round(v[0], 2) for k, v in phases.items() if v[1]})
         g = [t.grad.double() for t in (x, v, m)]
         del ws
         torch.cuda.empty_cache()

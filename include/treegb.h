@@ -84,6 +84,7 @@ typedef enum { TREE_F32 = 0, TREE_F64 = 1 } tree_dtype_t;
 
 /* tree_forces flags */
 #define TREE_FLAG_EMIT_LISTS 0x1 /* also store the interaction lists (tree_export_lists) */
+#define TREE_FLAG_LISTS_ONLY 0x2 /* with EMIT_LISTS: store the lists, skip the force evaluation (a may be NULL) */
 
 typedef struct {
     double G;            /* gravitational constant (Eq. 1) */
@@ -185,7 +186,9 @@ tree_status_t tree_moments(TreeWorkspace *ws, const void *x, const void *m, void
  * (overwritten), phi [n] or NULL, both in the caller's particle order.
  * flags: TREE_FLAG_EMIT_LISTS additionally stores each group's PC and PP
  * lists in ws (extra device memory, allocated on first use, synchronises
- * the stream once to size it). */
+ * the stream once to size it); with TREE_FLAG_LISTS_ONLY as well it stores
+ * the lists and evaluates no forces (a and phi are then ignored and may be
+ * NULL) -- what the adjoint needs. */
 tree_status_t tree_forces(TreeWorkspace *ws, void *a, void *phi, int32_t flags, void *stream);
 
 /* Vector-Jacobian product of the last tree_forces (not part of the paper:

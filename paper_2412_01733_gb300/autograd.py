@@ -65,13 +65,13 @@ class TreeLeapfrog(torch.autograd.Function):
                 xn1 = xs[n + 1 - s0]
                 ws.build(xn1)
                 ws.moments(xn1, m)
-                ws.forces(emit_lists=True, want_phi=False)
+                ws.forces(lists_only=True)
                 ws.leapfrog_adjoint_step(xb, vb, ab, mb, tau, phi_bar=pb if n + 1 == K else None)
         # a_0 = F(x_0)
         x0 = ckpts[0][0]
         ws.build(x0)
         ws.moments(x0, m)
-        ws.forces(emit_lists=True, want_phi=False)
+        ws.forces(lists_only=True)
         ws.forces_adjoint(ab, pb if K == 0 else None, xb, mb)
         return xb, vb, mb, None, None, None, None
 

@@ -184,22 +184,24 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_force_vjp(const AdjArgs A) {
             Real q[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) q[k] = QUAD ? s_q[w][lane][k] : Real(0);
-            double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            // the group's (at most 64) targets are summed in the working precision;
+            // the per-group totals go to the FP64 accumulators
+            Real acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             for (int t = 0; t < cnt; ++t) {
                 const V4 p = s_tp[w][t];
                 const V4 b = s_tc[w][t];
                 Real gx, gy, gz, mb, qb[6];
                 pc_vjp<Real, QUAD>(p.x - a.x, p.y - a.y, p.z - a.z, b.x, b.y, b.z, b.w, a.w, q, eps2, gx, gy, gz,
                                    mb, qb);
-                acc[0] += (double)mb;
-                acc[1] -= (double)gx; acc[2] -= (double)gy; acc[3] -= (double)gz;
+                acc[0] += mb;
+                acc[1] -= gx; acc[2] -= gy; acc[3] -= gz;
 #pragma unroll
-                for (int k = 0; k < 6; ++k) acc[4 + k] += (double)qb[k];
+                for (int k = 0; k < 6; ++k) acc[4 + k] += qb[k];
             }
             const uint32_t c = s_si[w][lane];
 #pragma unroll
-            for (int k = 0; k < 10; ++k)
-                if (acc[k] != 0.0) atomicAdd(A.ccot + (int64_t)k * A.cap + c, A.G * acc[k]);
+            for (int k = 0; k < (QUAD ? 10 : 4); ++k)
+                if (acc[k] != Real(0)) atomicAdd(A.ccot + (int64_t)k * A.cap + c, A.G * (double)acc[k]);
         }
         __syncwarp();
     }
@@ -232,19 +234,19 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_force_vjp(const AdjArgs A) {
         if (lane < nt) {
             const V4 a = s_a[w][lane];
             const uint32_t j = s_si[w][lane];
-            double gxs = 0, gys = 0, gzs = 0, dms = 0;
+            Real gxs = 0, gys = 0, gzs = 0, dms = 0;
             for (int t = 0; t < cnt; ++t) {
                 if (s_ti[w][t] == j) continue;
                 const V4 p = s_tp[w][t];
                 const V4 b = s_tc[w][t];
                 Real gx, gy, gz, dm;
                 pp_vjp<Real>(a.x - p.x, a.y - p.y, a.z - p.z, b.x, b.y, b.z, b.w, a.w, eps2, gx, gy, gz, dm);
-                gxs += (double)gx; gys += (double)gy; gzs += (double)gz; dms += (double)dm;
+                gxs += gx; gys += gy; gzs += gz; dms += dm;
             }
-            atomicAdd(A.xg + j, A.G * gxs);
-            atomicAdd(A.xg + A.n + j, A.G * gys);
-            atomicAdd(A.xg + 2 * A.n + j, A.G * gzs);
-            atomicAdd(A.mg + j, A.G * dms);
+            atomicAdd(A.xg + j, A.G * (double)gxs);
+            atomicAdd(A.xg + A.n + j, A.G * (double)gys);
+            atomicAdd(A.xg + 2 * A.n + j, A.G * (double)gzs);
+            atomicAdd(A.mg + j, A.G * (double)dms);
         }
         __syncwarp();
     };

@@ -74,7 +74,7 @@ void free_all(TreeWorkspace *ws) {
                     ws->gkey, ws->gbucket, ws->gfirst, ws->plev, ws->ccount, ws->coff, ws->gscan_status,
                     ws->adj_cot, ws->adj_xt, ws->adj_xg, ws->adj_mg, ws->adj_ccot, ws->pleaf, ws->nparent,
                     ws->seg_off, ws->seg_cstart, ws->seg_bchunk, ws->seg_bfirst, ws->seg_part,
-                    ws->seg_digit_off};
+                    ws->seg_digit_off, ws->cmask};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ws->graph_exec) cudaGraphExecDestroy(ws->graph_exec);
@@ -263,6 +263,7 @@ tree_status_t tree_workspace_create(int64_t n_max, const TreeParams *p, TreeWork
               dalloc(&ws->gbucket, 64) && dalloc(&ws->gfirst, (size_t)ws->groups_max + 1) &&
               dalloc(&ws->plev, N) && dalloc(&ws->pleaf, N) && dalloc(&ws->nparent, NC) &&
               dalloc(&ws->ccount, (size_t)chunks_max) && dalloc(&ws->coff, (size_t)chunks_max) &&
+              dalloc(&ws->cmask, 2 * (size_t)chunks_max) &&
               dalloc(&ws->gscan_status, (size_t)(chunks_max / 2048 + 2)) &&
               dalloc(&ws->dmac, kLevels);
     ws->chunks_cap = chunks_max;
@@ -374,9 +375,11 @@ tree_status_t tree_set_segments(TreeWorkspace *ws, int64_t nseg, const int64_t *
     if (ok && chunks_need > ws->chunks_cap) {
         cudaFree(ws->ccount);
         cudaFree(ws->coff);
+        cudaFree(ws->cmask);
         cudaFree(ws->gscan_status);
-        ws->ccount = ws->coff = ws->gscan_status = nullptr;
+        ws->ccount = ws->coff = ws->cmask = ws->gscan_status = nullptr;
         ok = dalloc(&ws->ccount, (size_t)chunks_need) && dalloc(&ws->coff, (size_t)chunks_need) &&
+             dalloc(&ws->cmask, 2 * (size_t)chunks_need) &&
              dalloc(&ws->gscan_status, (size_t)(chunks_need / 2048 + 2));
         ws->chunks_cap = ok ? chunks_need : 0;
     }
@@ -520,11 +523,13 @@ tree_status_t tree_forces(TreeWorkspace *ws, void *a, void *phi, int32_t flags, 
     if (!ws) return TREE_ERR_ARG;
     if (!ws->has_moments) return TREE_ERR_STATE;
     if (ws->n == 0) return TREE_OK;
-    if (!a) return TREE_ERR_ARG;
+    const bool lists_only = (flags & TREE_FLAG_EMIT_LISTS) && (flags & TREE_FLAG_LISTS_ONLY);
+    if (!a && !lists_only) return TREE_ERR_ARG;
     cudaStream_t s = as_stream(stream);
     if (flags & TREE_FLAG_EMIT_LISTS) {
         tree_status_t st = build_lists(ws, s);
         if (st != TREE_OK) return st;
+        if (lists_only) return TREE_OK;
     }
     WalkOut out{a, phi, nullptr, 0.0};
     return walk(ws, kWalkForce, out, s);

@@ -74,20 +74,39 @@ __device__ void box_from_minmax(double (&lo)[3], double (&hi)[3], DevBox *box) {
     box->unit = ldexp(1.0, k - kBits);
 }
 
-__global__ void k_box_final(const double *__restrict__ part, int nblocks, DevBox *box) {
-    if (threadIdx.x != 0) return;
+// One block: each thread folds a strided share of the partials, then the
+// block folds the threads (min and max are exact in any order).
+__global__ void __launch_bounds__(256) k_box_final(const double *__restrict__ part, int nblocks, DevBox *box) {
+    __shared__ double sh[6][8];
     double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
-    for (int b = 0; b < nblocks; ++b) {
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
         for (int d = 0; d < 3; ++d) {
             lo[d] = fmin(lo[d], part[b * 8 + d]);
             hi[d] = fmax(hi[d], part[b * 8 + 3 + d]);
         }
     }
-    box_from_minmax(lo, hi, box);
+    for (int d = 0; d < 3; ++d) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+            hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int d = 0; d < 3; ++d) { sh[d][warp] = lo[d]; sh[3 + d][warp] = hi[d]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = fmin(lo[d], sh[d][w]);
+                hi[d] = fmax(hi[d], sh[3 + d][w]);
+            }
+        box_from_minmax(lo, hi, box);
+    }
 }
 
 cudaError_t launch_box_final(TreeWorkspace *ws, int nblocks, cudaStream_t s) {
-    k_box_final<<<1, 32, 0, s>>>(ws->part, nblocks, ws->box);
+    k_box_final<<<1, 256, 0, s>>>(ws->part, nblocks, ws->box);
     ws->launches += 1;
     return cudaGetLastError();
 }

@@ -134,6 +134,7 @@ struct TreeWorkspace {
     uint32_t *pleaf = nullptr;         // leaf node of every sorted particle
     uint32_t *nparent = nullptr;       // parent of every node (root: itself)
     uint32_t *ccount = nullptr, *coff = nullptr;  // groups starting in each Gs chunk / their offsets
+    uint32_t *cmask = nullptr;         // group-start flags of each chunk, two 32-bit slices per chunk
     uint32_t *gscan_status = nullptr;  // look-back words of the chunk scan
     int64_t walk_grid = 0;             // resident walk blocks (persistent grid)
     int walk_grid_key = -1;

@@ -69,7 +69,9 @@ __device__ __forceinline__ uint32_t chunk_seg(const uint32_t *__restrict__ cstar
     return lo;
 }
 
-// One warp per chunk: number of groups that start inside it.
+// One warp per chunk: number of groups that start inside it (count pass,
+// which also keeps the start flags of every 32-particle slice in cmask), then
+// the group starts themselves (write pass, from cmask).
 template <bool WRITE>
 __global__ void __launch_bounds__(256) k_group_chunks(const uint64_t *__restrict__ skey, const uint8_t *__restrict__ plev,
                                                       const uint32_t *__restrict__ pleaf,
@@ -79,7 +81,8 @@ __global__ void __launch_bounds__(256) k_group_chunks(const uint64_t *__restrict
                                                       const int64_t *__restrict__ seg_off,
                                                       const uint32_t *__restrict__ cstart, int64_t nseg,
                                                       uint32_t *__restrict__ ccount, const uint32_t *__restrict__ coff,
-                                                      uint32_t *__restrict__ gfirst, const uint32_t *__restrict__ ctr) {
+                                                      uint32_t *__restrict__ cmask, uint32_t *__restrict__ gfirst,
+                                                      const uint32_t *__restrict__ ctr) {
     const int lane = threadIdx.x & 31;
     const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (c >= nchunks) return;
@@ -93,9 +96,16 @@ __global__ void __launch_bounds__(256) k_group_chunks(const uint64_t *__restrict
     uint32_t total = 0;
     for (int64_t off = 0; off < gs; off += 32) {
         const int64_t i = s0 + off + lane;
-        const bool st = off + lane < gs && i < s1 &&
-                        group_starts(skey, plev, pleaf, nparent, ncount, i, s0, delta, cmax);
-        const uint32_t b = __ballot_sync(0xffffffffu, st);
+        uint32_t b;
+        bool st;
+        if (WRITE) {
+            b = cmask[2 * c + (off >> 5)];
+            st = (b >> lane) & 1u;
+        } else {
+            st = off + lane < gs && i < s1 && group_starts(skey, plev, pleaf, nparent, ncount, i, s0, delta, cmax);
+            b = __ballot_sync(0xffffffffu, st);
+            if (lane == 0) cmask[2 * c + (off >> 5)] = b;
+        }
         if (WRITE && st) gfirst[base + total + __popc(b & lanemask_lt())] = (uint32_t)i;
         total += __popc(b);
     }
@@ -144,12 +154,12 @@ cudaError_t launch_groups(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
     const uint32_t cmax = 128u * (uint32_t)gs;
     k_group_chunks<false><<<wb, 256, 0, s>>>(ws->key, ws->plev, ws->pleaf, ws->nparent, ws->ncount, cmax, n, gs,
                                             ws->p.group_split, nchunks, ws->seg_off, ws->seg_cstart, ws->nseg, ws->ccount,
-                                            nullptr, nullptr, ws->ctr);
+                                            nullptr, ws->cmask, nullptr, ws->ctr);
     k_group_scan<<<(unsigned)tiles, kGScanThreads, 0, s>>>(ws->ccount, ws->coff, nchunks, ws->gscan_status, ws->ctr,
                                                           ws->dstatus);
     k_group_chunks<true><<<wb, 256, 0, s>>>(ws->key, ws->plev, ws->pleaf, ws->nparent, ws->ncount, cmax, n, gs,
                                            ws->p.group_split, nchunks, ws->seg_off, ws->seg_cstart, ws->nseg, nullptr,
-                                           ws->coff, ws->gfirst, ws->ctr);
+                                           ws->coff, ws->cmask, ws->gfirst, ws->ctr);
     ws->launches += 4;
     return cudaGetLastError();
 }

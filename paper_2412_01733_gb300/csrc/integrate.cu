@@ -121,11 +121,19 @@ __global__ void __launch_bounds__(256) k_diag_partial(const Real *__restrict__ x
     }
 }
 
-__global__ void k_diag_final(const double *__restrict__ part, int nb, double *out) {
+// One block of 256 threads: 32 threads per component each add every 32nd
+// partial, then one thread per component adds their 32 sums (fixed order).
+__global__ void __launch_bounds__(256) k_diag_final(const double *__restrict__ part, int nb, double *out) {
+    const int c = threadIdx.x & 7, j = threadIdx.x >> 3;  // 32 lanes per component
+    double r = 0;
+    for (int b = j; b < nb; b += 32) r += part[b * 8 + c];
+    __shared__ double sh[8][33];
+    sh[c][j] = r;
+    __syncthreads();
     if (threadIdx.x < 8) {
-        double r = 0;
-        for (int b = 0; b < nb; ++b) r += part[b * 8 + threadIdx.x];
-        out[threadIdx.x] = r;
+        double t = 0;
+        for (int k = 0; k < 32; ++k) t += sh[threadIdx.x][k];
+        out[threadIdx.x] = t;
     }
 }
 
@@ -138,7 +146,7 @@ cudaError_t launch_diagnostics(TreeWorkspace *ws, const void *x, const void *v, 
     else
         k_diag_partial<float><<<nb, 256, 0, s>>>((const float *)x, (const float *)v, (const float *)m,
                                                  (const float *)phi, n, ws->part);
-    k_diag_final<<<1, 32, 0, s>>>(ws->part, nb, out);
+    k_diag_final<<<1, 256, 0, s>>>(ws->part, nb, out);
     ws->launches += 2;
     return cudaGetLastError();
 }

@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
                     }
                 }
             } else if (np == 16) {
-#pragma unroll 4
+#pragma unroll 8
                 for (int k = 0; k < 16; ++k) {
                     const float4 a = stF[5 * k], b = stF[5 * k + 1];
 #pragma unroll
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
             const int np = (ns + 1) >> 1;
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
             if (np == 16) {
-#pragma unroll 2
+#pragma unroll 4
                 for (int k = 0; k < 16; ++k) {
                     const float4 a = stF[5 * k], b = stF[5 * k + 1];
                     const float4 c = QUAD ? stF[5 * k + 2] : z4, d = QUAD ? stF[5 * k + 3] : z4,

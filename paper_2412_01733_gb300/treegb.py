@@ -20,6 +20,7 @@ TREE_OK, TREE_ERR_ARG, TREE_ERR_CUDA, TREE_ERR_ALLOC, TREE_ERR_CAPACITY, TREE_ER
 DEV_NONFINITE, DEV_STACK, DEV_NODES, DEV_TIMEOUT, DEV_LIST = 0x01, 0x02, 0x04, 0x08, 0x10
 F32, F64 = 0, 1
 FLAG_EMIT_LISTS = 0x1
+FLAG_LISTS_ONLY = 0x2
 PHASES = ("box", "keys", "sort", "octree", "gather", "moments", "walk", "lists", "diag", "direct", "adjoint")
 
 
@@ -294,8 +295,14 @@ class Workspace:
         self._vec(x, n, "x"); self._scal(m, n, "m")
         _check("tree_moments", lib().tree_moments(self._h, _ptr(x), _ptr(m), _stream()))
 
-    def forces(self, a=None, phi=None, emit_lists=False, want_phi=True):
+    def forces(self, a=None, phi=None, emit_lists=False, want_phi=True, lists_only=False):
+        """Tree forces of the last build (a (3, n), phi (n,)); emit_lists also stores the
+        interaction lists; lists_only stores them without evaluating forces (returns None, None)."""
         n = self.n
+        if lists_only:
+            _check("tree_forces", lib().tree_forces(self._h, None, None, FLAG_EMIT_LISTS | FLAG_LISTS_ONLY,
+                                                    _stream()))
+            return None, None
         if a is None:
             a = torch.empty((3, n), dtype=self.dtype, device="cuda")
         if phi is None and want_phi:
