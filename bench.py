@@ -46,7 +46,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM bytes per walk launch from ncu (dram__bytes_read.sum + write.sum) on the
 # N = 1e7 galaxy case of the same kernel, per particle (scaled by N below);
 # None when the kernel has changed since the counters were taken.
-WALK_DRAM_BYTES_PER_PARTICLE = 1037
+WALK_DRAM_BYTES_PER_PARTICLE = 1019
 
 
 def _args():
@@ -240,13 +240,21 @@ def run_ours(a):
         xh = x.cpu().pin_memory(); vh = v.cpu().pin_memory(); mh = m.cpu().pin_memory()
         ah = acc.cpu().pin_memory(); dh = torch.empty(8, dtype=torch.float64).pin_memory()
 
+        part_ev = []
+
         def e2e_step():
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
             x.copy_(xh, non_blocking=True); v.copy_(vh, non_blocking=True)
             m.copy_(mh, non_blocking=True); acc.copy_(ah, non_blocking=True)
+            ev[1].record(stream)
             ws.leapfrog_step(x, v, m, acc, TAU, phi=phi)
             ws.diagnostics(x, v, m, phi, out=diag)
+            ev[2].record(stream)
             xh.copy_(x, non_blocking=True); vh.copy_(v, non_blocking=True)
             ah.copy_(acc, non_blocking=True); dh.copy_(diag, non_blocking=True)
+            ev[3].record(stream)
+            part_ev.append(ev)
 
         e2e_step()
         torch.cuda.synchronize()
@@ -262,8 +270,12 @@ def run_ours(a):
         barrier()
         ck_e2e = clocks_e2e.stop()
         te = max_over_ranks(h0.elapsed_time(h1) / 1e3)
+        timed_ev = part_ev[-a.steps:]
+        split = {k: sum(ev[i].elapsed_time(ev[i + 1]) for ev in timed_ev) / a.steps
+                 for i, k in enumerate(("h2d_ms", "step_ms", "d2h_ms"))}
         out["e2e"] = {"value": world * n * a.steps / te, "unit": UNIT,
-                      "h2d_bytes_per_step": 40 * n, "d2h_bytes_per_step": 36 * n + 64, "clocks": ck_e2e}
+                      "h2d_bytes_per_step": 40 * n, "d2h_bytes_per_step": 36 * n + 64, "clocks": ck_e2e,
+                      "per_step": {k: round(v, 2) for k, v in split.items()}}
         del xh, vh, mh, ah, dh
         # same-GPU FP64 plain path: one force evaluation (build + moments + walk) on the same state
         x64, m64 = x.double().contiguous(), m.double().contiguous()
