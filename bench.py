@@ -123,6 +123,32 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# ----------------------------------------------------------------- ranks
+# One process per GPU.  The galaxy step is one problem, so N ranks run N
+# independent replicas (seed + rank); an ensemble is split by system with no
+# exchange at all.  Timing is the maximum over ranks.
+def max_over_ranks(v, world, device):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_share(sizes, rank, world):
+    """Systems of an ensemble owned by `rank`: largest first, each to the least
+    loaded rank (ties to the lower rank), so particle counts stay balanced."""
+    load = [0] * world
+    own = [[] for _ in range(world)]
+    for b in sorted(range(len(sizes)), key=lambda b: (-int(sizes[b]), b)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        own[r].append(b)
+        load[r] += int(sizes[b])
+    return sorted(own[rank])
+
+
 # ----------------------------------------------------------------- our arm
 def run_ours(a):
     import torch
@@ -143,13 +169,6 @@ def run_ours(a):
     def barrier():
         if world > 1:
             dist.barrier()
-
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     # each rank runs its own replica of the workload (independent seeds)
     x, v, m = inputs.galaxy(n, SEED + rank, device=dev, dtype=torch.float32)
@@ -188,7 +207,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     barrier()
     ck = clocks.stop()
-    t = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
     phases, launches = ws.timing_read()
     ws.timing(False)
     inf = ws.info()
@@ -269,7 +288,7 @@ def run_ours(a):
         torch.cuda.synchronize()
         barrier()
         ck_e2e = clocks_e2e.stop()
-        te = max_over_ranks(h0.elapsed_time(h1) / 1e3)
+        te = max_over_ranks(h0.elapsed_time(h1) / 1e3, world, dev)
         timed_ev = part_ev[-a.steps:]
         split = {k: sum(ev[i].elapsed_time(ev[i + 1]) for ev in timed_ev) / a.steps
                  for i, k in enumerate(("h2d_ms", "step_ms", "d2h_ms"))}
@@ -487,10 +506,27 @@ def study_ensemble(a):
     import numpy as np
     import torch
 
+    import torch.distributed as dist
+
     from paper_2412_01733_gb300 import build, inputs, treegb
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
     build.build()
     B, tau = 512, 0.005
-    x, v, m, off = inputs.ensemble(B, SEED, device="cuda", dtype=torch.float32)
+    x, v, m, off = inputs.ensemble(B, SEED, device=dev, dtype=torch.float32)
+    n_all = x.shape[1]
+    if world > 1:
+        # this rank's systems (no exchange between ranks)
+        own = rank_share(np.diff(off), rank, world)
+        idx = torch.cat([torch.arange(int(off[b]), int(off[b + 1]), device=dev) for b in own])
+        x, v, m = x[:, idx], v[:, idx], m[idx]
+        off = np.concatenate(([0], np.cumsum(np.diff(off)[own]))).astype(np.int64)
+        B = len(own)
     x, v, m = x.contiguous(), v.contiguous(), m.contiguous()
     n = x.shape[1]
     base = dict(eps=0.01, theta=0.6, order=2, kahan=1, leaf_cap=16, group_size=32)
@@ -518,31 +554,51 @@ def study_ensemble(a):
     for _ in range(W):
         ws.graph_launch()
     l0 = ws.launches()
-    ms_graph = timed(ws.graph_launch, K)
+    if world > 1:
+        dist.barrier()
+    ms_graph = max_over_ranks(timed(ws.graph_launch, K), world, dev)
     launches_per_step = (ws.launches() - l0) / K
     inf = ws.info()
 
     def eager():
         ws.leapfrog_step(x, v, m, acc, tau, phi=phi)
         ws.diagnostics(x, v, m, phi, out=diag)
-    ms_eager = timed(eager, max(3, K // 5))
+    ms_eager = max_over_ranks(timed(eager, max(3, K // 5)), world, dev)
     steps_run = W + K + max(3, K // 5)
     d1 = ws.diagnostics_segments(x, v, m, phi).cpu().numpy()
     e0_, e1_ = d0[:, 0] + d0[:, 1], d1[:, 0] + d1[:, 1]
     drift = np.abs(e1_ - e0_) / np.abs(e0_)
-    row = {"study": "ensemble", "clusters": B, "n": n, "eps": 0.01, "theta": 0.6, "order": "quadrupole",
+    if world > 1:
+        # per-cluster drifts from every rank
+        dt = torch.tensor(drift, dtype=torch.float64, device=dev)
+        parts = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in range(world)]
+        dist.all_gather(parts, dt.max().reshape(1))
+        drift_max = float(torch.stack(parts).max())
+    else:
+        drift_max = float(drift.max())
+    pairs = float(inf["pp_pairs"] + inf["pc_pairs"])
+    if world > 1:
+        tp = torch.tensor([pairs], dtype=torch.float64, device=dev)
+        dist.all_reduce(tp)
+        pairs = float(tp.item())
+    n, B = n_all, 512
+    row = {"study": "ensemble", "clusters": B, "n": n, "n_gpus": world, "scaling": "weak",
+           "eps": 0.01, "theta": 0.6, "order": "quadrupole",
            "dtype": "f32+kahan", "tau": tau, "autotuned": {"leaf_cap": best.leaf_cap, "group_size": best.group_size,
                                                            "stack_depth": best.stack_depth},
            "autotune_table": [list(r) for r in table], "autotune_s": tune_s,
            "graph": {"ms_per_step": ms_graph, "particles_per_s": n / (ms_graph / 1e3),
-                     "interactions_per_s": (inf["pp_pairs"] + inf["pc_pairs"]) / (ms_graph / 1e3),
+                     "interactions_per_s": pairs / (ms_graph / 1e3),
                      "kernels_per_step": launches_per_step, "steps": K},
            "eager": {"ms_per_step": ms_eager, "particles_per_s": n / (ms_eager / 1e3)},
-           "interactions_per_particle": (inf["pp_pairs"] + inf["pc_pairs"]) / n, "n_groups": inf["n_groups"],
-           "energy_drift_per_cluster": {"median": float(np.median(drift)), "max": float(drift.max()),
+           "interactions_per_particle": pairs / n, "n_groups (rank 0)": inf["n_groups"],
+           "energy_drift_per_cluster": {"median (rank 0)": float(np.median(drift)), "max": drift_max,
                                         "steps": steps_run},
            "status": ws.status()}
-    print(json.dumps(row), flush=True)
+    if rank == 0:
+        print(json.dumps(row), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def study_adjoint(a):
