@@ -68,6 +68,8 @@ def _args():
                          "adjoint: gradients through 16 KDK steps of Plummer N=262144 (times, FP32 vs FP64, "
                          "tree vs theta=0, finite differences)")
     ap.add_argument("--study-steps", type=int, default=100)
+    ap.add_argument("--err-samples", type=int, default=100000,
+                    help="particles whose tree force is checked against the GPU direct sum (extras)")
     ap.add_argument("--nvtx", action="store_true",
                     help="mark each timed step with an NVTX range named 'step' (for profiler selection)")
     return ap.parse_args()
@@ -194,17 +196,18 @@ def run_ours(a):
     torch.cuda.synchronize()
     ws.timing(True)
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    e0, e1 = evs[0], evs[-1]
     e0.record(stream)
-    for _ in range(a.steps):
+    for k in range(a.steps):
         if a.nvtx:
             torch.cuda.nvtx.range_push("step")
         step()
         if a.nvtx:
             torch.cuda.nvtx.range_pop()
-    e1.record(stream)
+        evs[k + 1].record(stream)
     torch.cuda.synchronize()
+    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(a.steps)]
     barrier()
     ck = clocks.stop()
     t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
@@ -230,10 +233,11 @@ def run_ours(a):
                 "flops_per_launch": flops, "pp_pairs": inf["pp_pairs"], "pc_pairs": inf["pc_pairs"],
                 "walk_ms": walk_s * 1e3}
     step_ms = t * 1e3 / a.steps
+    sem = statistics.stdev(per_step) / math.sqrt(len(per_step)) if len(per_step) > 1 else None
     breakdown = {k: round(ms / a.steps, 3) for k, (ms, c) in phases.items() if c}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-           "warmup": a.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+           "warmup": a.warmup, "ms_per_step": step_ms, "ms_per_step_sem": sem, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "n": n, "group_size": PARAMS["group_size"],
                       "leaf_cap": PARAMS["leaf_cap"], "kahan": True, "parallelism": f"replicas{world}",
@@ -246,14 +250,14 @@ def run_ours(a):
            "clocks": ck}
 
     if not a.no_extras:
-        # force error of the FP32 tree against the GPU direct sum (4096 sampled particles)
+        # force error of the FP32 tree against the GPU direct sum (sampled particles)
         g = torch.Generator().manual_seed(SEED)
-        tgt = torch.randint(0, n, (4096,), generator=g)
+        tgt = torch.randint(0, n, (min(n, a.err_samples),), generator=g)
         ad, _ = ws.direct(x, m, tgt, precision="f32")
         at = acc[:, tgt.to(dev)].double()
         err = ((at - ad).norm(dim=0) / ad.norm(dim=0)).cpu()
         out["force_err_vs_direct"] = {"median": float(err.median()), "p99": float(err.quantile(0.99)),
-                                      "max": float(err.max()), "samples": 4096,
+                                      "max": float(err.max()), "samples": int(tgt.numel()),
                                       "reference": "GPU direct sum, FP32 pairs, compensated, FP64 chunk totals"}
         # end to end through the C ABI with host-resident state
         xh = x.cpu().pin_memory(); vh = v.cpu().pin_memory(); mh = m.cpu().pin_memory()
@@ -477,6 +481,15 @@ def study_threads(a):
             print(json.dumps({"study": "threads", "n": n, "threads": M, "host_cpus": ncpu, "T_s": T, "T_sem": dT,
                               "S": S, "S_err": dS, "E": S / M, "E_err": dS / M}), flush=True)
         O.set_threads(ncpu)
+    # the direct sum of Eq. 1 (the paper's PP tool), N = 2^15, one thread and all
+    x, _, m = inputs.galaxy(1 << 15, SEED, dtype=torch.float64)
+    x, m = x.numpy(), m.numpy()
+    for M in (1, ncpu):
+        O.set_threads(M)
+        t0 = time.perf_counter()
+        O.direct(x, m, eps=PARAMS["eps"])
+        print(json.dumps({"study": "threads_direct", "n": 1 << 15, "threads": M, "T_s": time.perf_counter() - t0}),
+              flush=True)
     # efficiency against N at M = 4 threads (the paper's E(N) view), N = 2^17 .. 2^21
     for lg in range(17, 22):
         n = 1 << lg

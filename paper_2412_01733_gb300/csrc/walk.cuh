@@ -72,7 +72,7 @@ __host__ __device__ constexpr size_t walk_stage_bytes() {
 // staging arrays (float4 / 32-byte double4) stay aligned.
 template <typename Real>
 __host__ __device__ constexpr size_t walk_warp_bytes(int stack_depth) {
-    return (((size_t)(stack_depth + kPPCap + kPCCap + 64) * 4 + walk_stage_bytes<Real>()) + 31) & ~(size_t)31;
+    return (((size_t)(stack_depth + kPPCap + kPCCap + 32) * 4 + walk_stage_bytes<Real>()) + 31) & ~(size_t)31;
 }
 
 // --- pair terms ------------------------------------------------------------
@@ -238,8 +238,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
     uint32_t *stack = reinterpret_cast<uint32_t *>(wb + walk_stage_bytes<Real>());
     uint32_t *ppbuf = stack + SD;
     uint32_t *pcbuf = ppbuf + kPPCap;
-    int *mark = reinterpret_cast<int *>(pcbuf + kPCCap);
-    uint32_t *sidx = reinterpret_cast<uint32_t *>(mark + 32);  // sorted index of each staged near source
+    uint32_t *sidx = pcbuf + kPCCap;  // sorted index of each staged near source
     const uint32_t lt = lanemask_lt();
 
     const V4 *__restrict__ spos = reinterpret_cast<const V4 *>(A.spos);
@@ -516,16 +515,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
         const uint32_t take = avail < 32u ? avail : 32u;
         const bool contrib = lane < nr && excl0 < take;
         const int nfull = __popc(__ballot_sync(0xffffffffu, lane < nr && incl0 <= take));
-        mark[lane] = -1;
-        __syncwarp();
-        if (contrib) mark[excl0] = lane;
-        __syncwarp();
-        int owner = mark[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, owner, o);
-            if (lane >= o) owner = max(owner, y);
-        }
+        // the contributing ranges are lanes 0..k-1 with increasing starts excl0:
+        // lane t belongs to the last one whose start is <= t
+        const uint32_t starts = __reduce_or_sync(0xffffffffu, contrib ? (1u << excl0) : 0u);
+        const int owner = __popc(starts & (lt | (1u << lane))) - 1;
         const uint32_t e_own = __shfl_sync(0xffffffffu, e, owner & 31);
         const uint32_t x_own = __shfl_sync(0xffffffffu, excl0, owner & 31);
         const bool act = (uint32_t)lane < take;
@@ -574,31 +567,35 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
         }
         max_top = max(max_top, (uint32_t)top);
 
-        // near leaves
+        // near leaves (most steps of a deep walk have none)
         const uint32_t lm = __ballot_sync(0xffffffffu, nleaf);
-        if (MODE == kWalkEmit) {
-            if (nleaf) A.pp_list[pp_base + n_ppl + __popc(lm & lt)] = (int32_t)node;
-        }
-        n_ppl += __popc(lm);
-        const uint32_t lc = nleaf ? lk.y : 0u;
-        const bool big = lc > (uint32_t)kMaxLeafSmall;
-        const uint32_t sc = big ? 0u : lc;
-        const uint32_t incl2 = warp_incl_scan(sc, lane);
-        const uint32_t tot2 = __shfl_sync(0xffffffffu, incl2, 31);
-        n_pp += __reduce_add_sync(0xffffffffu, lc);
-        if (MODE == kWalkForce) {
-            if (nleaf && !big)
-                for (uint32_t c = 0; c < lc; ++c) ppbuf[npp + (incl2 - lc) + c] = lk.x + c;
-            npp += (int)tot2;
-            __syncwarp();
-            uint32_t bm = __ballot_sync(0xffffffffu, big);
-            while (bm) {
-                const int b = __ffs(bm) - 1;
-                bm &= bm - 1;
-                const uint32_t f = __shfl_sync(0xffffffffu, lk.x, b);
-                const uint32_t c = __shfl_sync(0xffffffffu, lk.y, b);
-                for (uint32_t o = 0; o < c; o += 32) eval_pp_range(f + o, (int)min(32u, c - o));
+        if (lm) {
+            if (MODE == kWalkEmit) {
+                if (nleaf) A.pp_list[pp_base + n_ppl + __popc(lm & lt)] = (int32_t)node;
             }
+            n_ppl += __popc(lm);
+            const uint32_t lc = nleaf ? lk.y : 0u;
+            const bool big = lc > (uint32_t)kMaxLeafSmall;
+            const uint32_t sc = big ? 0u : lc;
+            const uint32_t incl2 = warp_incl_scan(sc, lane);
+            const uint32_t tot2 = __shfl_sync(0xffffffffu, incl2, 31);
+            n_pp += __reduce_add_sync(0xffffffffu, lc);
+            if (MODE == kWalkForce) {
+                if (nleaf && !big)
+                    for (uint32_t c = 0; c < lc; ++c) ppbuf[npp + (incl2 - lc) + c] = lk.x + c;
+                npp += (int)tot2;
+                __syncwarp();
+                uint32_t bm = __ballot_sync(0xffffffffu, big);
+                while (bm) {
+                    const int b = __ffs(bm) - 1;
+                    bm &= bm - 1;
+                    const uint32_t f = __shfl_sync(0xffffffffu, lk.x, b);
+                    const uint32_t c = __shfl_sync(0xffffffffu, lk.y, b);
+                    for (uint32_t o = 0; o < c; o += 32) eval_pp_range(f + o, (int)min(32u, c - o));
+                }
+            }
+        }
+        if (MODE == kWalkForce) {
             if (npc >= 32) {
                 eval_pc_list(pcbuf, 32);
                 const int r = npc - 32;
