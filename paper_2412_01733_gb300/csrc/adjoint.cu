@@ -154,8 +154,9 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_force_vjp(const AdjArgs A) {
             if (QUAD) {
                 const V4 b = momB[c];
                 const V2 cc = momC[c];
-                s_q[w][lane][0] = b.x; s_q[w][lane][1] = b.y; s_q[w][lane][2] = b.z;
-                s_q[w][lane][3] = b.w; s_q[w][lane][4] = cc.x; s_q[w][lane][5] = cc.y;
+                const Real qs = sizeof(Real) == 4 ? Real(-1) : Real(1);  // FP32 walk copies hold -Q
+                s_q[w][lane][0] = qs * b.x; s_q[w][lane][1] = qs * b.y; s_q[w][lane][2] = qs * b.z;
+                s_q[w][lane][3] = qs * b.w; s_q[w][lane][4] = qs * cc.x; s_q[w][lane][5] = qs * cc.y;
             }
         }
         __syncwarp();

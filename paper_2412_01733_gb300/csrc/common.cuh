@@ -123,8 +123,8 @@ struct TreeWorkspace {
     uint2 *nlink = nullptr;            // internal: {child, nchild}; leaf: {first, count}
     double *mom64 = nullptr;           // [10][node_cap]: M, Rx, Ry, Rz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz
     void *mom_a = nullptr;             // Vec4: (Rx, Ry, Rz, M)
-    void *mom_b = nullptr;             // Vec4: (Qxx, Qyy, Qzz, Qxy)
-    void *mom_c = nullptr;             // Vec2: (Qxz, Qyz)
+    void *mom_b = nullptr;             // Vec4: (Qxx, Qyy, Qzz, Qxy); FP32 copies hold -Q
+    void *mom_c = nullptr;             // Vec2: (Qxz, Qyz); FP32 copies hold -Q
     // status and statistics
     int32_t *dstatus = nullptr;
     unsigned long long *stats = nullptr;

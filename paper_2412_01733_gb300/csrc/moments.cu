@@ -11,7 +11,7 @@
 //   M = sum M_k,  R = c + sum M_k (R_k - c) / M,
 //   Q = sum_k [Q_k + M_k (3 d_k d_k^T - |d_k|^2 I)].
 // Massless cells get R = c, Q = 0.  The FP64 results are kept, and rounded
-// copies in the walk's precision are packed for the walk.
+// copies in the walk's precision are packed for the walk (FP32: -Q).
 #include "common.cuh"
 
 namespace treegb {
@@ -94,9 +94,11 @@ __global__ void __launch_bounds__(256) k_moments_level(
         Q_[3][node] = qxy; Q_[4][node] = qxz; Q_[5][node] = qyz;
         typename Vec4<Real>::T a, b;
         typename Vec2<Real>::T c;
+        // the FP32 walk copies hold -Q (the sign its packed pair terms want)
+        const double qs = sizeof(Real) == 4 ? -1.0 : 1.0;
         a.x = (Real)Rx; a.y = (Real)Ry; a.z = (Real)Rz; a.w = (Real)M;
-        b.x = (Real)qxx; b.y = (Real)qyy; b.z = (Real)qzz; b.w = (Real)qxy;
-        c.x = (Real)qxz; c.y = (Real)qyz;
+        b.x = (Real)(qs * qxx); b.y = (Real)(qs * qyy); b.z = (Real)(qs * qzz); b.w = (Real)(qs * qxy);
+        c.x = (Real)(qs * qxz); c.y = (Real)(qs * qyz);
         mom_a[node] = a; mom_b[node] = b; mom_c[node] = c;
     }
 }

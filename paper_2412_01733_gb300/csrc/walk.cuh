@@ -151,8 +151,8 @@ __device__ __forceinline__ void pp_pair(float2 nx, float2 ny, float2 nz, float2 
     acc[3] = __ffma2_rn(neg1, mr, acc[3]);
 }
 
-// PC for two cells.  With u = R - r_i (= -y) and the staged negated
-// quadrupole Qn = -Q, w = Qn u equals Q y, u.w = -(y.Q.y), and the terms of
+// PC for two cells.  With u = R - r_i (= -y) and the negated quadrupole
+// Qn = -Q (the FP32 cell copies store -Q), w = Qn u equals Q y, u.w = -(y.Q.y), and the terms of
 // pc_term become a = [M/r^3 - 5/2 (u.w)/r^7] u + w/r^5, phi = -M/r + 1/2 (u.w)/r^5.
 template <bool QUAD, bool SOFT>
 __device__ __forceinline__ void pc_pair(float2 nx, float2 ny, float2 nz, const float4 &A, const float4 &B,
@@ -420,9 +420,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
                     if (QUAD) { b = momB[cell]; c = momC[cell]; }
                 }
                 q[sl] = a.x; q[2 + sl] = a.y; q[4 + sl] = a.z; q[6 + sl] = a.w;
-                if (QUAD) {
-                    q[8 + sl] = -b.x; q[10 + sl] = -b.y; q[12 + sl] = -b.z; q[14 + sl] = -b.w;
-                    q[16 + sl] = -c.x; q[18 + sl] = -c.y;
+                if (QUAD) {  // the FP32 cell copies already hold -Q
+                    q[8 + sl] = b.x; q[10 + sl] = b.y; q[12 + sl] = b.z; q[14 + sl] = b.w;
+                    q[16 + sl] = c.x; q[18 + sl] = c.y;
                 }
             }
             __syncwarp();
@@ -558,14 +558,16 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
 
         // children of opened cells: one stack entry per opened cell
         const uint32_t om = __ballot_sync(0xffffffffu, open);
-        const int no = __popc(om);
-        if (top + no > SD) {
-            overflow = true;
-        } else {
-            if (open) stack[top + __popc(om & lt)] = lk.x | ((lk.y - 1u) << 29);
-            top += no;
+        if (om) {
+            const int no = __popc(om);
+            if (top + no > SD) {
+                overflow = true;
+            } else {
+                if (open) stack[top + __popc(om & lt)] = lk.x | ((lk.y - 1u) << 29);
+                top += no;
+            }
+            max_top = max(max_top, (uint32_t)top);
         }
-        max_top = max(max_top, (uint32_t)top);
 
         // near leaves (most steps of a deep walk have none)
         const uint32_t lm = __ballot_sync(0xffffffffu, nleaf);
