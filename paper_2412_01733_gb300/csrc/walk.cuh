@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
                     }
                 }
             } else if (np == 16) {
-#pragma unroll 8
+#pragma unroll 16
                 for (int k = 0; k < 16; ++k) {
                     const float4 a = stF[5 * k], b = stF[5 * k + 1];
 #pragma unroll
