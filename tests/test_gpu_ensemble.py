@@ -253,3 +253,37 @@ def test_ensemble_full_size_sampled(orc):
             ref = orc.tree_forces(_np64(xb), _np64(mb), eps=0.01, theta=0.6, lcap=16, gs=32, quad=True)
             e = np.linalg.norm(_np64(aa) - ref.a, axis=0) / np.linalg.norm(ref.a, axis=0)
             assert np.median(e) <= 1e-5 and e.max() <= 1e-4
+
+
+def test_ensemble_fp64_equals_each_system_alone():
+    """The FP64 plain walk with systems: bit-identical to each system alone."""
+    tg = _tg()
+    x, v, m, off = _mixed_ensemble(seed=53)
+    xg, mg = x.cuda().contiguous(), m.cuda().contiguous()
+    p = dict(P, precision="f64")
+    ws, a, phi = _run(tg, xg, mg, off, **p)
+    for b0, b1 in zip(off[:-1], off[1:]):
+        wa, aa, pa = _run(tg, xg[:, b0:b1].contiguous(), mg[b0:b1].contiguous(), **p)
+        assert torch.equal(a[:, b0:b1], aa) and torch.equal(phi[b0:b1], pa)
+
+
+def test_many_systems_two_segment_passes():
+    """300 systems (> 256: the system index takes two sort passes), sizes 1..40."""
+    tg = _tg()
+    sizes = np.random.default_rng(7).integers(1, 41, size=300)
+    xs, ms = [], []
+    for b, nb in enumerate(sizes):
+        x, _, m = inputs.plummer(int(nb), 100 + b)
+        xs.append(x * (0.5 + (b % 5))); ms.append(m)
+    off = np.concatenate(([0], np.cumsum(sizes))).astype(np.int64)
+    xg, mg = torch.cat(xs, 1).float().cuda().contiguous(), torch.cat(ms).float().cuda().contiguous()
+    ws, a, phi = _run(tg, xg, mg, off, **P)
+    ex = ws.export_tree()
+    perm = ex["perm"].cpu().numpy()
+    # every system's particles stay in its own sorted range
+    for b0, b1 in zip(off[:-1], off[1:]):
+        assert perm[b0:b1].min() >= b0 and perm[b0:b1].max() < b1
+    for b in (0, 150, 299):
+        b0, b1 = int(off[b]), int(off[b + 1])
+        wa, aa, pa = _run(tg, xg[:, b0:b1].contiguous(), mg[b0:b1].contiguous(), **P)
+        assert torch.equal(a[:, b0:b1], aa) and torch.equal(phi[b0:b1], pa)
