@@ -60,13 +60,14 @@ def _args():
                     help="particles of the oracle's bounded sample (same galaxy recipe)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the main leg only (no FP64 leg, error check, e2e, CPU baseline)")
-    ap.add_argument("--study", choices=["theta", "threads", "ensemble", "adjoint"], default=None,
+    ap.add_argument("--study", choices=["theta", "threads", "ensemble", "adjoint", "plain"], default=None,
                     help="theta: precision study on the Plummer N=2^20 config (force error vs direct sum, "
                          "energy drift, FP32 vs FP64 time per force, theta in {0.4,0.5,0.7,1.0}); "
                          "threads: T(M), speedup and efficiency of the CPU oracle vs host threads M; "
                          "ensemble: 512 Plummer clusters in one build, autotuned, one CUDA graph per step; "
                          "adjoint: gradients through 16 KDK steps of Plummer N=262144 (times, FP32 vs FP64, "
-                         "tree vs theta=0, finite differences)")
+                         "tree vs theta=0, finite differences); plain: the FP64 Plummer N=16384 configuration "
+                         "(tree vs direct error, 10 KDK steps, energy and momentum drift, GPU vs oracle)")
     ap.add_argument("--study-steps", type=int, default=100)
     ap.add_argument("--err-samples", type=int, default=100000,
                     help="particles whose tree force is checked against the GPU direct sum (extras)")
@@ -717,8 +718,55 @@ def study_adjoint(a):
     print(json.dumps(row), flush=True)
 
 
+def study_plain(a):
+    """Plain FP64 configuration: Plummer N = 16384 (G = M = a = 1), eps = 0.01, theta = 0.7, monopole cells,
+    leaf <= 16; one force evaluation and 10 KDK steps of tau = 0.01 on the GPU (FP64 walk) and with the
+    oracle.  Reports the tree force error against the FP64 direct sum (all particles), the GPU against the
+    oracle, and the energy and momentum drift of both runs."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2412_01733_gb300 import build, inputs, treegb
+    build.build()
+    n, eps, theta, tau, K = 16384, 0.01, 0.7, 0.01, 10
+    x, v, m = inputs.plummer(n, SEED)
+    xn, vn, mn = x.numpy(), v.numpy(), m.numpy()
+    kw = dict(eps=eps, theta=theta, lcap=16, gs=32, quad=False)
+    ad, pd = O.direct(xn, mn, eps=eps)
+    ref = O.tree_forces(xn, mn, **kw)
+    ws = treegb.Workspace(n, precision="f64", eps=eps, theta=theta, order=0, leaf_cap=16, group_size=32)
+    xg, vg, mg = x.cuda().contiguous(), v.cuda().contiguous(), m.cuda().contiguous()
+    ag, pg = ws.accel(xg, mg)
+    agn = ag.cpu().numpy()
+    e_tree = np.linalg.norm(ref.a - ad, axis=0) / np.linalg.norm(ad, axis=0)
+    e_gpu = np.linalg.norm(agn - ref.a, axis=0) / np.linalg.norm(ref.a, axis=0)
+    d0 = O.diagnostics(xn, vn, mn, ref.phi)
+    acc = lambda xx: O.tree_accel(xx, mn, **kw)
+    xo, vo, ao, po = O.kdk(xn, vn, mn, tau, K, acc, a0=(ref.a, ref.phi))
+    d1 = O.diagnostics(xo, vo, mn, po)
+    g0 = ws.diagnostics(xg, vg, mg, pg).cpu().numpy()
+    for _ in range(K):
+        ws.leapfrog_step(xg, vg, mg, ag, tau, phi=pg)
+    g1 = ws.diagnostics(xg, vg, mg, pg).cpu().numpy()
+    pscale = float(np.sum(mn * np.linalg.norm(vn, axis=0)))
+    row = {"study": "plain", "n": n, "eps": eps, "theta": theta, "order": "monopole", "precision": "f64",
+           "tree_vs_direct": {"median": float(np.median(e_tree)), "p99": float(np.quantile(e_tree, 0.99)),
+                              "max": float(e_tree.max())},
+           "gpu_vs_oracle": {"median": float(np.median(e_gpu)), "max": float(e_gpu.max())},
+           "oracle_kdk": {"energy_drift": abs(d1["etot"] - d0["etot"]) / abs(d0["etot"]),
+                          "momentum_drift": float(np.abs(d1["P"] - d0["P"]).max()) / pscale},
+           "gpu_kdk": {"energy_drift": float(abs((g1[0] + g1[1]) - (g0[0] + g0[1])) / abs(g0[0] + g0[1])),
+                       "momentum_drift": float(np.abs(g1[2:5] - g0[2:5]).max()) / pscale},
+           "gpu_vs_oracle_after_kdk": float(np.abs(xg.cpu().numpy() - xo).max()),
+           "status": ws.status()}
+    print(json.dumps(row), flush=True)
+
+
 def main():
     a = _args()
+    if a.study == "plain":
+        return study_plain(a)
     if a.study == "theta":
         return study_theta(a)
     if a.study == "adjoint":
