@@ -772,7 +772,7 @@ tree_status_t tree_autotune(const TreeParams *base, int64_t nseg, const int64_t 
                 float t = 0.f;
                 cudaEventElapsedTime(&t, e0, e1);
                 st = tree_get_status(ws, &dev, 1);
-                if (st == TREE_ERR_DEVICE) st = TREE_OK;  // judged below
+                if (st == TREE_ERR_DEVICE) st = TREE_OK;  // the status bits decide below
                 if (st != TREE_OK) break;
                 if (dev == 0) ms = (double)t / reps;  // a candidate that overflowed its stack does not count
                 if (table && used < rows) {

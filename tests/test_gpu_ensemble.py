@@ -6,7 +6,7 @@ a system equal (bit for bit, after renumbering the nodes) those of a
 workspace holding that system alone, and its FP32 forces, leapfrog states and
 per-system diagnostics agree with the lone run -- bit-identical where the
 arithmetic is the same, to FP64 rounding for the reductions -- and with the
-FP64 oracle of each system (spec tolerance).  Also: a captured CUDA
+FP64 oracle of each system (median relative error <= 1e-5, max <= 1e-4).  Also: a captured CUDA
 graph of a step replays the eager steps bit for bit; the autotuner returns
 the fastest valid candidate.
 """
