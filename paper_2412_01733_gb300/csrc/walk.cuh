@@ -28,7 +28,7 @@ namespace treegb {
 
 constexpr int kWalkWarps = 4;                      // warps per block
 constexpr int kPPCap = 32 + 32 * kMaxLeafSmall;    // PP buffer entries per warp
-constexpr int kPCCap = 64;                         // PC buffer entries per warp
+constexpr int kPCCap = 32 + 32 * 8;                // PC buffer entries per warp (a step adds <= 32 x 8)
 
 struct WalkArgs {
     int64_t n;
@@ -544,6 +544,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
         const bool far = act && d2 >= sD[level];
         const bool nleaf = act && !far && leaf;
         const bool open = act && !far && !leaf;
+        // A child's box lies inside its parent's, so it is at least as far from
+        // the group: when an opened cell already meets its children's threshold
+        // (d2 >= D[level + 1]), all its children are far and go to the far list
+        // without being popped and tested one by one.
+        const bool allfar = open && d2 >= sD[min(level + 1, kMaxLevel)];
 
         // far cells
         const uint32_t fm = __ballot_sync(0xffffffffu, far);
@@ -555,15 +560,31 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
             if (far) A.pc_list[pc_base + n_pc + __popc(fm & lt)] = (int32_t)node;
         }
         n_pc += nf;
+        const uint32_t am = __ballot_sync(0xffffffffu, allfar);
+        if (am) {
+            const uint32_t cc = allfar ? lk.y : 0u;
+            const uint32_t incl = warp_incl_scan(cc, lane);
+            const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+            if (MODE == kWalkForce) {
+                if (allfar)
+                    for (uint32_t c = 0; c < cc; ++c) pcbuf[npc + (incl - cc) + c] = lk.x + c;
+                npc += (int)tot;
+            } else if (MODE == kWalkEmit) {
+                if (allfar)
+                    for (uint32_t c = 0; c < cc; ++c) A.pc_list[pc_base + n_pc + (incl - cc) + c] = (int32_t)(lk.x + c);
+            }
+            n_pc += tot;
+        }
 
-        // children of opened cells: one stack entry per opened cell
-        const uint32_t om = __ballot_sync(0xffffffffu, open);
+        // children of the other opened cells: one stack entry per opened cell
+        const bool push = open && !allfar;
+        const uint32_t om = __ballot_sync(0xffffffffu, push);
         if (om) {
             const int no = __popc(om);
             if (top + no > SD) {
                 overflow = true;
             } else {
-                if (open) stack[top + __popc(om & lt)] = lk.x | ((lk.y - 1u) << 29);
+                if (push) stack[top + __popc(om & lt)] = lk.x | ((lk.y - 1u) << 29);
                 top += no;
             }
             max_top = max(max_top, (uint32_t)top);
@@ -599,9 +620,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
         }
         if (MODE == kWalkForce) {
             if (npc >= 32) {
-                eval_pc_list(pcbuf, 32);
-                const int r = npc - 32;
-                uint32_t t = lane < r ? pcbuf[32 + lane] : 0;
+                __syncwarp();
+                const int ntile = npc >> 5;
+                for (int t = 0; t < ntile; ++t) eval_pc_list(pcbuf + 32 * t, 32);
+                const int r = npc & 31;
+                uint32_t t = lane < r ? pcbuf[32 * ntile + lane] : 0;
                 __syncwarp();
                 if (lane < r) pcbuf[lane] = t;
                 __syncwarp();
