@@ -74,7 +74,7 @@ void free_all(TreeWorkspace *ws) {
                     ws->gkey, ws->gbucket, ws->gfirst, ws->plev, ws->ccount, ws->coff, ws->gscan_status,
                     ws->adj_cot, ws->adj_xt, ws->adj_xg, ws->adj_mg, ws->adj_ccot, ws->pleaf, ws->nparent,
                     ws->seg_off, ws->seg_cstart, ws->seg_bchunk, ws->seg_bfirst, ws->seg_part,
-                    ws->seg_digit_off, ws->cmask};
+                    ws->seg_digit_off, ws->cmask, ws->morder, ws->mbucket};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ws->graph_exec) cudaGraphExecDestroy(ws->graph_exec);
@@ -256,6 +256,7 @@ tree_status_t tree_workspace_create(int64_t n_max, const TreeParams *p, TreeWork
               dalloc(&ws->part, (size_t)kMaxBlocksReduce * 8) && dalloc(&ws->box, 1) &&
               dalloc((unsigned char **)&ws->spos, N * v4) && dalloc(&ws->nfirst, NC) && dalloc(&ws->ncount, NC) &&
               dalloc(&ws->ngeo, NC) && dalloc(&ws->nlink, NC) && dalloc(&ws->mom64, 10 * NC) &&
+              dalloc(&ws->morder, NC) && dalloc(&ws->mbucket, 3 * kMomBuckets + 1) &&
               dalloc((unsigned char **)&ws->mom_a, NC * v4) && dalloc((unsigned char **)&ws->mom_b, NC * v4) &&
               dalloc((unsigned char **)&ws->mom_c, NC * v2) && dalloc(&ws->dstatus, 1) &&
               dalloc(&ws->stats, kStatCount) && dalloc(&ws->gstat, (size_t)ws->groups_max) &&

@@ -221,11 +221,29 @@ cudaError_t launch_box(TreeWorkspace *ws, const void *x, int64_t n, cudaStream_t
 }
 
 // ============================================================== keys + histograms
-// q_d = min(2^21-1, floor(fl(x_d - lo_d) * 2^(21-k))): the subtraction is the
-// only rounding (the scaling is by a power of two).  The key interleaves
-// q_x, q_y, q_z (x highest).  The same pass counts the eight 8-bit digits of
-// every key for the radix sort (warp-aggregated shared-memory atomics).
+// q_d = min(2^21-1, floor(fl(x_d - lo_d) * 2^(21-k))), negatives to 0: the
+// FP64 subtraction is the only rounding (the scaling is by a power of two).
+// The key interleaves q_x, q_y, q_z (x highest).  The same pass counts the
+// eight 8-bit digits of every key for the radix sort (warp-aggregated
+// shared-memory atomics).
 // SEG: every particle is quantised in the box of its own segment.
+
+// The floor and both clamps are one saturating round-down conversion
+// (cvt.rmi.u32.f64 clamps out-of-range values, negatives to 0) and an integer
+// min; a NaN lands in some in-range cell (the box pass has already raised
+// TREE_DEV_NONFINITE for it).
+__device__ __forceinline__ uint32_t quantize(double x, double lo, double sc) {
+    return min(__double2uint_rd(__dmul_rn(__dsub_rn(x, lo), sc)), (1u << kBits) - 1u);
+}
+// FP32 coordinates: x sc and lo sc are exact in FP64 (a float, or the box
+// corner, times a power of two stays far inside the FP64 range), so one fused
+// multiply-add, x sc - lo sc, rounds (x - lo) sc exactly as the FP64
+// subtraction followed by the exact scaling does: the same q_d with a third
+// of the FP64 instructions (the FP64 pipe runs at 1/64 of the FP32 rate here).
+__device__ __forceinline__ uint32_t quantize(float x, double lo, double sc) {
+    return min(__double2uint_rd(fma((double)x, sc, -(lo * sc))), (1u << kBits) - 1u);
+}
+
 template <typename Real, bool SEG>
 __global__ void __launch_bounds__(256) k_keys(const Real *__restrict__ x, int64_t n,
                                               const DevBox *__restrict__ box, const int64_t *__restrict__ seg_off,
@@ -235,7 +253,6 @@ __global__ void __launch_bounds__(256) k_keys(const Real *__restrict__ x, int64_
     for (int i = threadIdx.x; i < kSortPasses * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
     __syncthreads();
     const double lo0 = box->lo[0], lo1 = box->lo[1], lo2 = box->lo[2], scale = box->scale;
-    const double qmax = (double)((1u << kBits) - 1u);
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
@@ -252,13 +269,7 @@ __global__ void __launch_bounds__(256) k_keys(const Real *__restrict__ x, int64_
             }
             uint32_t q[3];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                double diff = __dsub_rn((double)x[d * n + i], lo[d]);
-                double f = floor(__dmul_rn(diff, sc));
-                if (!(f >= 0.0)) f = 0.0;  // also catches NaN
-                if (f > qmax) f = qmax;
-                q[d] = (uint32_t)f;
-            }
+            for (int d = 0; d < 3; ++d) q[d] = quantize(x[d * n + i], lo[d], sc);
             k = morton3(q[0], q[1], q[2]);
             key[i] = k;
         }

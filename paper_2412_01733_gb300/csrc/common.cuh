@@ -13,6 +13,8 @@ namespace treegb {
 constexpr int kBits = 21;          // bits per axis of the quantised coordinates
 constexpr int kMaxLevel = 21;      // deepest octree level
 constexpr int kLevels = 22;        // levels 0..21
+constexpr int kMomLeafBuckets = 17;                          // moment buckets of leaves (count 1..16, 17+)
+constexpr int kMomBuckets = kMomLeafBuckets + 8 * kMaxLevel;  // + internal cells by (level, nchild)
 constexpr int kSortThreads = 256;  // onesweep block
 constexpr int kSortItems = 16;     // keys per thread
 constexpr int kSortTile = kSortThreads * kSortItems;
@@ -122,6 +124,8 @@ struct TreeWorkspace {
     uint4 *ngeo = nullptr;             // {cx, cy, cz, level | leaf << 8}
     uint2 *nlink = nullptr;            // internal: {child, nchild}; leaf: {first, count}
     double *mom64 = nullptr;           // [10][node_cap]: M, Rx, Ry, Rz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz
+    uint32_t *morder = nullptr;        // nodes in moment-bucket order [node_cap]
+    uint32_t *mbucket = nullptr;       // moment buckets: counts, offsets (+ total), cursors
     void *mom_a = nullptr;             // Vec4: (Rx, Ry, Rz, M)
     void *mom_b = nullptr;             // Vec4: (Qxx, Qyy, Qzz, Qxy); FP32 copies hold -Q
     void *mom_c = nullptr;             // Vec2: (Qxz, Qyz); FP32 copies hold -Q

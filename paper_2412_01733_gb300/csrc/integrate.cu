@@ -77,34 +77,39 @@ cudaError_t launch_kick_drift_box(TreeWorkspace *ws, void *x, void *v, const voi
 // E_kin = 1/2 sum m v^2, W = 1/2 sum m phi, P = sum m v, L = sum m x cross v.
 // Fixed grid and fixed reduction order: deterministic.
 // Per-particle products in the input precision, summed in that precision
-// over runs of 32 particles per thread, then accumulated in FP64.
+// over runs of 32 particles per thread, then accumulated in FP64.  A run is
+// its own loop, so the FP64 flush issues once per run (folded into the
+// particle loop as a predicated branch, it issued for every particle).
+template <typename Real>
+__device__ __forceinline__ void diag_accumulate(const Real *__restrict__ x, const Real *__restrict__ v,
+                                                const Real *__restrict__ m, const Real *__restrict__ phi, int64_t n,
+                                                int64_t i, int64_t end, int64_t step, double (&q)[8]) {
+    while (i < end) {
+        Real r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = 0; k < 32 && i < end; ++k, i += step) {
+            const Real mi = m[i];
+            const Real x0 = x[i], x1 = x[n + i], x2 = x[2 * n + i];
+            const Real v0 = v[i], v1 = v[n + i], v2 = v[2 * n + i];
+            r[0] += mi * (v0 * v0 + v1 * v1 + v2 * v2);
+            if (phi) r[1] += mi * phi[i];
+            r[2] += mi * v0; r[3] += mi * v1; r[4] += mi * v2;
+            r[5] += mi * (x1 * v2 - x2 * v1);
+            r[6] += mi * (x2 * v0 - x0 * v2);
+            r[7] += mi * (x0 * v1 - x1 * v0);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) q[c] += (double)r[c];
+    }
+}
+
 template <typename Real>
 __global__ void __launch_bounds__(256) k_diag_partial(const Real *__restrict__ x, const Real *__restrict__ v,
                                                       const Real *__restrict__ m, const Real *__restrict__ phi,
                                                       int64_t n, double *__restrict__ part) {
     __shared__ double sh[8][8];
     double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    Real r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int run = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const Real mi = m[i];
-        const Real x0 = x[i], x1 = x[n + i], x2 = x[2 * n + i];
-        const Real v0 = v[i], v1 = v[n + i], v2 = v[2 * n + i];
-        r[0] += mi * (v0 * v0 + v1 * v1 + v2 * v2);
-        if (phi) r[1] += mi * phi[i];
-        r[2] += mi * v0; r[3] += mi * v1; r[4] += mi * v2;
-        r[5] += mi * (x1 * v2 - x2 * v1);
-        r[6] += mi * (x2 * v0 - x0 * v2);
-        r[7] += mi * (x0 * v1 - x1 * v0);
-        if (++run == 32) {
-#pragma unroll
-            for (int c = 0; c < 8; ++c) { q[c] += (double)r[c]; r[c] = 0; }
-            run = 0;
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 8; ++c) q[c] += (double)r[c];
+    diag_accumulate(x, v, m, phi, n, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, n,
+                    (int64_t)gridDim.x * blockDim.x, q);
     q[0] *= 0.5;
     q[1] *= 0.5;
 #pragma unroll
@@ -164,26 +169,7 @@ __global__ void __launch_bounds__(256) k_diag_chunks(const Real *__restrict__ x,
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         const uint4 c = chunks[ch];
         double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        Real r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        int run = 0;
-        for (int64_t i = c.x + threadIdx.x; i < (int64_t)c.y; i += blockDim.x) {
-            const Real mi = m[i];
-            const Real x0 = x[i], x1 = x[n + i], x2 = x[2 * n + i];
-            const Real v0 = v[i], v1 = v[n + i], v2 = v[2 * n + i];
-            r[0] += mi * (v0 * v0 + v1 * v1 + v2 * v2);
-            if (phi) r[1] += mi * phi[i];
-            r[2] += mi * v0; r[3] += mi * v1; r[4] += mi * v2;
-            r[5] += mi * (x1 * v2 - x2 * v1);
-            r[6] += mi * (x2 * v0 - x0 * v2);
-            r[7] += mi * (x0 * v1 - x1 * v0);
-            if (++run == 32) {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) { q[k] += (double)r[k]; r[k] = 0; }
-                run = 0;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) q[k] += (double)r[k];
+        diag_accumulate(x, v, m, phi, n, (int64_t)c.x + threadIdx.x, (int64_t)c.y, (int64_t)blockDim.x, q);
         q[0] *= 0.5;
         q[1] *= 0.5;
 #pragma unroll
