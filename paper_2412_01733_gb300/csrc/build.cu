@@ -273,10 +273,11 @@ __global__ void __launch_bounds__(256) k_keys(const Real *__restrict__ x, int64_
             k = morton3(q[0], q[1], q[2]);
             key[i] = k;
         }
+        const uint32_t vm = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
         for (int p = 0; p < kSortPasses; ++p) {
-            uint32_t dg = valid ? (uint32_t)((k >> (8 * p)) & 0xffu) : 0x100u;
-            uint32_t peers = __match_any_sync(0xffffffffu, dg);
+            const uint32_t dg = (uint32_t)((k >> (8 * p)) & 0xffu);
+            const uint32_t peers = match_digit8(dg, valid ? vm : ~vm);
             if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&sh[p][dg], (uint32_t)__popc(peers));
         }
     }
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(256) k_hist_scan(uint32_t *hist) {
 
 // ============================================================== onesweep pass
 // One block sorts one tile of kSortTile keys by the 8-bit digit at `shift`:
-// warp-level ranking with match_any (stable: a warp owns a contiguous
+// warp-level ranking with digit-matching ballots (stable: a warp owns a contiguous
 // segment and walks it item by item, lanes in order), per-digit decoupled
 // look-back across tiles for the global position, then a scatter through
 // shared memory so that global writes are runs of equal digits.
@@ -325,7 +326,7 @@ __device__ __forceinline__ uint32_t sort_digit(uint64_t k, uint32_t v, int shift
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(
+__global__ void __launch_bounds__(kSortThreads, MODE == kPassSeg ? 2 : 3) k_onesweep(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t n, int shift, const uint32_t *__restrict__ digit_off,
     uint32_t *status, uint32_t *ticket, int32_t *dstatus, const int64_t *__restrict__ seg_off, int64_t nseg) {
@@ -338,25 +339,35 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint32_t tile = S.tile;
     const int64_t base = (int64_t)tile * kSortTile;
 
+    // the digit of item i (0x100 past the end): kept for segment passes (a
+    // binary search), recomputed from the key otherwise (fewer live registers)
+    constexpr int kDg = MODE == kPassSeg ? kSortItems : 1;
     uint64_t k[kSortItems];
-    uint32_t v[kSortItems], dg[kSortItems], rk[kSortItems];
+    uint32_t v[kSortItems], dgs[kDg], rk[kSortItems];
     const int64_t wbase = base + warp * (kSortItems * 32);
+    auto digit = [&](int i) -> uint32_t {
+        if (MODE == kPassSeg) return dgs[i % kDg];
+        return wbase + i * 32 + lane < n ? (uint32_t)((k[i] >> shift) & 0xffu) : 0x100u;
+    };
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
         const int64_t pos = wbase + i * 32 + lane;
         if (pos < n) {
             k[i] = kin[pos];
             v[i] = MODE == kPassFirst ? (uint32_t)pos : vin[pos];
-            dg[i] = sort_digit<MODE>(k[i], v[i], shift, seg_off, nseg);
+            if (MODE == kPassSeg) dgs[i % kDg] = sort_digit<MODE>(k[i], v[i], shift, seg_off, nseg);
         } else {
-            k[i] = 0; v[i] = 0; dg[i] = 0x100u;
+            k[i] = 0; v[i] = 0;
+            if (MODE == kPassSeg) dgs[i % kDg] = 0x100u;
         }
     }
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
-        const uint32_t d = dg[i];
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t d = digit(i);
+        const bool ok = d < 0x100u;
+        const uint32_t vm = __ballot_sync(0xffffffffu, ok);
+        const uint32_t peers = match_digit8(d, ok ? vm : ~vm);
         uint32_t cnt = 0;
         if (d < 0x100u) cnt = S.whist[warp][d];
         __syncwarp();
@@ -413,7 +424,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
-        const uint32_t d = dg[i];
+        const uint32_t d = digit(i);
         if (d < 0x100u) {
             const uint32_t p = S.start[d] + S.whist[warp][d] + rk[i];
             S.keys[p] = k[i];
@@ -460,12 +471,17 @@ cudaError_t launch_sort(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
     const size_t smem = sizeof(SortSmem);
     static bool attr_done[64] = {};
     if (ws->device < 64 && !attr_done[ws->device]) {
-        cudaError_t e = cudaFuncSetAttribute(k_onesweep<kPassFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_onesweep<kPassKey>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_onesweep<kPassSeg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // the key passes fit three blocks per SM (registers and shared memory)
+        // when the carveout gives shared memory all it can
+        const void *fn[3] = {(const void *)k_onesweep<kPassFirst>, (const void *)k_onesweep<kPassKey>,
+                             (const void *)k_onesweep<kPassSeg>};
+        cudaError_t e = cudaSuccess;
+        for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
+            e = cudaFuncSetAttribute(fn[f], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(fn[f], cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+        }
         if (e != cudaSuccess) return e;
         attr_done[ws->device] = true;
     }

@@ -189,6 +189,20 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+// Lanes of the (full) warp whose 8-bit digit d equals this lane's, from one
+// ballot per digit bit; `same` starts the match (e.g. the lanes with the same
+// validity).  The ballots run on the integer pipes, where a match.any of the
+// whole value would queue on the address-divergence unit.
+__device__ __forceinline__ uint32_t match_digit8(uint32_t d, uint32_t same) {
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        same &= bit ? bal : ~bal;
+    }
+    return same;
+}
+
 // Spread the low 21 bits of v so that bit b lands at bit 3b.
 __host__ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
     uint64_t x = v & 0x1fffffu;
