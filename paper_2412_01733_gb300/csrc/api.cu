@@ -74,7 +74,7 @@ void free_all(TreeWorkspace *ws) {
                     ws->gkey, ws->gbucket, ws->gfirst, ws->plev, ws->ccount, ws->coff, ws->gscan_status,
                     ws->adj_cot, ws->adj_xt, ws->adj_xg, ws->adj_mg, ws->adj_ccot, ws->pleaf, ws->nparent,
                     ws->seg_off, ws->seg_cstart, ws->seg_bchunk, ws->seg_bfirst, ws->seg_part,
-                    ws->seg_digit_off, ws->cmask, ws->morder, ws->mbucket};
+                    ws->seg_digit_off, ws->cmask, ws->morder, ws->mbucket, ws->xm};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ws->graph_exec) cudaGraphExecDestroy(ws->graph_exec);
@@ -254,7 +254,8 @@ tree_status_t tree_workspace_create(int64_t n_max, const TreeParams *p, TreeWork
               dalloc(&ws->sort_status, (size_t)(kSortPasses + kSegPassesMax) * ws->sort_tiles_max * kRadix) &&
               dalloc(&ws->level_status, (size_t)kLevels * ws->level_tiles_max) && dalloc(&ws->ctr, kCtrCount) &&
               dalloc(&ws->part, (size_t)kMaxBlocksReduce * 8) && dalloc(&ws->box, 1) &&
-              dalloc((unsigned char **)&ws->spos, N * v4) && dalloc(&ws->nfirst, NC) && dalloc(&ws->ncount, NC) &&
+              dalloc((unsigned char **)&ws->spos, N * v4) && dalloc((unsigned char **)&ws->xm, N * v4) &&
+              dalloc(&ws->nfirst, NC) && dalloc(&ws->ncount, NC) &&
               dalloc(&ws->ngeo, NC) && dalloc(&ws->nlink, NC) && dalloc(&ws->mom64, 10 * NC) &&
               dalloc(&ws->morder, NC) && dalloc(&ws->mbucket, 3 * kMomBuckets + 1) &&
               dalloc((unsigned char **)&ws->mom_a, NC * v4) && dalloc((unsigned char **)&ws->mom_b, NC * v4) &&
@@ -609,7 +610,7 @@ tree_status_t leapfrog_step(TreeWorkspace *ws, void *x, void *v, const void *m, 
     // Eqs. 2-3 fused with the box of the new positions
     {
         PhaseScope ph(ws, TREE_PHASE_BOX, s);
-        TRY_CUDA(launch_kick_drift_box(ws, x, v, a, tau, n, s));
+        TRY_CUDA(launch_kick_drift_box(ws, x, v, a, m, tau, n, s));
     }
     // Eq. 4: tree at r^{n+1}
     {
@@ -628,7 +629,7 @@ tree_status_t leapfrog_step(TreeWorkspace *ws, void *x, void *v, const void *m, 
     ws->built = true;
     {
         PhaseScope ph(ws, TREE_PHASE_GATHER, s);
-        TRY_CUDA(launch_gather(ws, x, m, n, s));
+        TRY_CUDA(launch_gather_packed(ws, n, s));
     }
     {
         PhaseScope ph(ws, TREE_PHASE_MOMENTS, s);

@@ -117,8 +117,9 @@ cudaError_t launch_box_final(TreeWorkspace *ws, int nblocks, cudaStream_t s) {
 // per segment folds its chunks.
 template <typename Real, bool KICK>
 __global__ void __launch_bounds__(256) k_box_chunks(Real *__restrict__ x, Real *__restrict__ v,
-                                                    const Real *__restrict__ a, Real half_tau, Real tau, int64_t n,
-                                                    const uint4 *__restrict__ chunks, int64_t nchunks,
+                                                    const Real *__restrict__ a, const Real *__restrict__ m,
+                                                    typename Vec4<Real>::T *__restrict__ xm, Real half_tau, Real tau,
+                                                    int64_t n, const uint4 *__restrict__ chunks, int64_t nchunks,
                                                     double *__restrict__ part, int32_t *dstatus) {
     __shared__ double sh[6][8];
     const Real big = sizeof(Real) == 4 ? (Real)FLT_MAX : (Real)DBL_MAX;
@@ -128,6 +129,7 @@ __global__ void __launch_bounds__(256) k_box_chunks(Real *__restrict__ x, Real *
         Real mn[3] = {big, big, big}, mx[3] = {-big, -big, -big};
         bool bad = false;
         for (int64_t i = ch.x + threadIdx.x; i < (int64_t)ch.y; i += blockDim.x) {
+            Real xn[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 Real xx;
@@ -139,9 +141,15 @@ __global__ void __launch_bounds__(256) k_box_chunks(Real *__restrict__ x, Real *
                 } else {
                     xx = x[d * n + i];
                 }
+                xn[d] = xx;
                 if (!isfinite(xx)) { bad = true; continue; }
                 mn[d] = min(mn[d], xx);
                 mx[d] = max(mx[d], xx);
+            }
+            if (KICK) {
+                typename Vec4<Real>::T p;
+                p.x = xn[0]; p.y = xn[1]; p.z = xn[2]; p.w = m[i];
+                xm[i] = p;
             }
         }
         if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(dstatus, TREE_DEV_NONFINITE);
@@ -184,26 +192,28 @@ __global__ void k_box_seg_final(const double *__restrict__ part, const uint32_t 
 }
 
 template <typename Real>
-static cudaError_t box_seg_impl(TreeWorkspace *ws, Real *x, Real *v, const Real *a, double tau, int64_t n,
-                                bool kick, cudaStream_t s) {
+static cudaError_t box_seg_impl(TreeWorkspace *ws, Real *x, Real *v, const Real *a, const Real *m, double tau,
+                                int64_t n, bool kick, cudaStream_t s) {
+    using V4 = typename Vec4<Real>::T;
     const int nb = grid_for(ws->seg_nbchunk * 256, 256, 152 * 16);
     if (kick)
-        k_box_chunks<Real, true><<<nb, 256, 0, s>>>(x, v, a, (Real)(0.5 * tau), (Real)tau, n, ws->seg_bchunk,
-                                                   ws->seg_nbchunk, ws->seg_part, ws->dstatus);
+        k_box_chunks<Real, true><<<nb, 256, 0, s>>>(x, v, a, m, (V4 *)ws->xm, (Real)(0.5 * tau), (Real)tau, n,
+                                                   ws->seg_bchunk, ws->seg_nbchunk, ws->seg_part, ws->dstatus);
     else
-        k_box_chunks<Real, false><<<nb, 256, 0, s>>>(x, nullptr, nullptr, Real(0), Real(0), n, ws->seg_bchunk,
-                                                    ws->seg_nbchunk, ws->seg_part, ws->dstatus);
+        k_box_chunks<Real, false><<<nb, 256, 0, s>>>(x, nullptr, nullptr, nullptr, nullptr, Real(0), Real(0), n,
+                                                    ws->seg_bchunk, ws->seg_nbchunk, ws->seg_part, ws->dstatus);
     k_box_seg_final<<<grid_for(ws->nseg, 128, 1 << 20), 128, 0, s>>>(ws->seg_part, ws->seg_bfirst, ws->nseg,
                                                                      ws->box);
     ws->launches += 2;
     return cudaGetLastError();
 }
 
-cudaError_t launch_box_segments(TreeWorkspace *ws, void *x, void *v, const void *a, double tau, int64_t n,
-                                bool kick, cudaStream_t s) {
+cudaError_t launch_box_segments(TreeWorkspace *ws, void *x, void *v, const void *a, const void *m, double tau,
+                                int64_t n, bool kick, cudaStream_t s) {
     if (ws->p.precision == TREE_F64)
-        return box_seg_impl<double>(ws, (double *)x, (double *)v, (const double *)a, tau, n, kick, s);
-    return box_seg_impl<float>(ws, (float *)x, (float *)v, (const float *)a, tau, n, kick, s);
+        return box_seg_impl<double>(ws, (double *)x, (double *)v, (const double *)a, (const double *)m, tau, n,
+                                    kick, s);
+    return box_seg_impl<float>(ws, (float *)x, (float *)v, (const float *)a, (const float *)m, tau, n, kick, s);
 }
 
 template <typename Real>
@@ -215,7 +225,8 @@ static cudaError_t box_impl(TreeWorkspace *ws, const Real *x, int64_t n, cudaStr
 }
 
 cudaError_t launch_box(TreeWorkspace *ws, const void *x, int64_t n, cudaStream_t s) {
-    if (ws->nseg > 1) return launch_box_segments(ws, const_cast<void *>(x), nullptr, nullptr, 0.0, n, false, s);
+    if (ws->nseg > 1)
+        return launch_box_segments(ws, const_cast<void *>(x), nullptr, nullptr, nullptr, 0.0, n, false, s);
     if (ws->p.precision == TREE_F64) return box_impl(ws, (const double *)x, n, s);
     return box_impl(ws, (const float *)x, n, s);
 }
@@ -538,16 +549,29 @@ __global__ void k_tree_init(uint32_t *ctr, uint32_t *nfirst, uint32_t *ncount, u
     }
 }
 
-// First index in [lo, hi) whose octant digit at `shift` is >= o (keys in the
-// range share their higher digits, so the digit is non-decreasing).
-__device__ __forceinline__ uint32_t digit_lower_bound(const uint64_t *__restrict__ skey, uint32_t lo,
-                                                      uint32_t hi, int shift, uint32_t o) {
-    while (lo < hi) {
-        uint32_t mid = lo + ((hi - lo) >> 1);
-        if ((uint32_t)((skey[mid] >> shift) & 7u) < o) lo = mid + 1;
-        else hi = mid;
+// Octant boundaries of a node's sorted range [first, first + count), count
+// >= 1: b[o] = first index whose octant digit at `shift` is >= o, o = 1..7
+// (keys in the range share their higher digits, so the digit is
+// non-decreasing).  Seven branchless lower-bound searches advance in lock
+// step, so each step issues seven independent loads: a large node costs
+// log2(count) load latencies, not seven times that.
+__device__ __forceinline__ void octant_bounds(const uint64_t *__restrict__ skey, uint32_t first, uint32_t count,
+                                              int shift, uint32_t (&b)[9]) {
+    uint32_t base[7];
+#pragma unroll
+    for (int o = 0; o < 7; ++o) base[o] = first;
+    uint32_t len = count;
+    while (len > 1) {
+        const uint32_t half = len >> 1;
+#pragma unroll
+        for (int o = 0; o < 7; ++o)
+            if ((uint32_t)((skey[base[o] + half] >> shift) & 7u) < (uint32_t)(o + 1)) base[o] += half;
+        len -= half;
     }
-    return lo;
+#pragma unroll
+    for (int o = 0; o < 7; ++o) b[o + 1] = base[o] + ((uint32_t)((skey[base[o]] >> shift) & 7u) < (uint32_t)(o + 1));
+    b[0] = first;
+    b[8] = first + count;
 }
 
 // Level L: every node decides leaf/internal; internal nodes find their
@@ -591,11 +615,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(
         uint32_t b[9];
         uint32_t nch = 0;
         if (internal) {
-            const uint32_t e = first + count;
-            b[0] = first;
-            b[8] = e;
-#pragma unroll
-            for (int o = 1; o < 8; ++o) b[o] = digit_lower_bound(skey, b[o - 1], e, shift, (uint32_t)o);
+            octant_bounds(skey, first, count, shift, b);
 #pragma unroll
             for (int o = 0; o < 8; ++o) nch += b[o + 1] > b[o] ? 1u : 0u;
         }
@@ -666,6 +686,25 @@ __global__ void __launch_bounds__(256) k_gather(const Real *__restrict__ x, cons
         p.w = m[i];
         spos[s] = p;
     }
+}
+
+// From the packed (x, y, z, m) copy the kick-drift pass wrote: one aligned
+// vector load per particle.
+template <typename V4>
+__global__ void __launch_bounds__(256) k_gather_packed(const V4 *__restrict__ xm, const uint32_t *__restrict__ idx,
+                                                       int64_t n, V4 *__restrict__ spos) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+        spos[s] = xm[idx[s]];
+}
+
+cudaError_t launch_gather_packed(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
+    int nb = grid_for(n, 256, 152 * 16);
+    if (ws->p.precision == TREE_F64)
+        k_gather_packed<double4a><<<nb, 256, 0, s>>>((const double4a *)ws->xm, ws->idx, n, (double4a *)ws->spos);
+    else
+        k_gather_packed<float4><<<nb, 256, 0, s>>>((const float4 *)ws->xm, ws->idx, n, (float4 *)ws->spos);
+    ws->launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gather(TreeWorkspace *ws, const void *x, const void *m, int64_t n, cudaStream_t s) {

@@ -119,6 +119,8 @@ struct TreeWorkspace {
     int64_t graph_launches = 0, graph_n = 0;
     // sorted particles (float4 / double4a)
     void *spos = nullptr;
+    // packed (x, y, z, m) in caller order, written by the kick-drift pass
+    void *xm = nullptr;
     // nodes
     uint32_t *nfirst = nullptr, *ncount = nullptr;
     uint4 *ngeo = nullptr;             // {cx, cy, cz, level | leaf << 8}
@@ -320,14 +322,15 @@ namespace treegb {
 // build.cu
 cudaError_t launch_box(TreeWorkspace *ws, const void *x, int64_t n, cudaStream_t s);
 cudaError_t launch_box_final(TreeWorkspace *ws, int nblocks, cudaStream_t s);
-cudaError_t launch_box_segments(TreeWorkspace *ws, void *x, void *v, const void *a, double tau, int64_t n,
-                                bool kick, cudaStream_t s);
+cudaError_t launch_box_segments(TreeWorkspace *ws, void *x, void *v, const void *a, const void *m, double tau,
+                                int64_t n, bool kick, cudaStream_t s);
 cudaError_t launch_keys(TreeWorkspace *ws, const void *x, int64_t n, cudaStream_t s);
 cudaError_t launch_sort(TreeWorkspace *ws, int64_t n, cudaStream_t s);
 cudaError_t launch_octree(TreeWorkspace *ws, int64_t n, cudaStream_t s);
 // groups.cu
 cudaError_t launch_groups(TreeWorkspace *ws, int64_t n, cudaStream_t s);
 cudaError_t launch_gather(TreeWorkspace *ws, const void *x, const void *m, int64_t n, cudaStream_t s);
+cudaError_t launch_gather_packed(TreeWorkspace *ws, int64_t n, cudaStream_t s);
 cudaError_t launch_export_tree(TreeWorkspace *ws, int64_t nn, int32_t *level, uint32_t *corner, uint32_t *first,
                                uint32_t *count, int32_t *child, int32_t *nchild, cudaStream_t s);
 // moments.cu
@@ -348,7 +351,7 @@ cudaError_t launch_adjoint(TreeWorkspace *ws, const void *abar, const void *phib
 cudaError_t launch_adjoint_step(TreeWorkspace *ws, void *xbar, void *vbar, void *abar, void *mbar,
                                 const void *phibar, double tau, cudaStream_t s);
 // integrate.cu
-cudaError_t launch_kick_drift_box(TreeWorkspace *ws, void *x, void *v, const void *a, double tau,
+cudaError_t launch_kick_drift_box(TreeWorkspace *ws, void *x, void *v, const void *a, const void *m, double tau,
                                   int64_t n, cudaStream_t s);
 cudaError_t launch_diagnostics(TreeWorkspace *ws, const void *x, const void *v, const void *m,
                                const void *phi, int64_t n, double *out, cudaStream_t s);

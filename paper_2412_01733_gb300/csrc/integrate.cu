@@ -13,10 +13,14 @@ namespace treegb {
 // ============================================================== kick + drift + box
 // v += tau/2 a (Eq. 2); x += tau v (Eq. 3); per-block FP64 min/max of the new
 // positions for the next tree (the same partial layout as the box kernel).
+// The new positions also go, with the masses, into a packed (x, y, z, m) copy
+// in caller order, from which the tree's gather reads one aligned vector per
+// particle instead of four scattered scalars.
 template <typename Real>
 __global__ void __launch_bounds__(256) k_kick_drift_box(Real *__restrict__ x, Real *__restrict__ v,
-                                                        const Real *__restrict__ a, Real half_tau, Real tau,
-                                                        int64_t n, double *__restrict__ part,
+                                                        const Real *__restrict__ a, const Real *__restrict__ m,
+                                                        typename Vec4<Real>::T *__restrict__ xm, Real half_tau,
+                                                        Real tau, int64_t n, double *__restrict__ part,
                                                         int32_t *dstatus) {
     __shared__ double sh[6][8];
     const Real big = sizeof(Real) == 4 ? (Real)FLT_MAX : (Real)DBL_MAX;
@@ -24,16 +28,21 @@ __global__ void __launch_bounds__(256) k_kick_drift_box(Real *__restrict__ x, Re
     bool bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
+        Real xn[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const Real vv = fma(half_tau, a[d * n + i], v[d * n + i]);
             const Real xx = fma(tau, vv, x[d * n + i]);
             v[d * n + i] = vv;
             x[d * n + i] = xx;
+            xn[d] = xx;
             if (!isfinite(xx)) { bad = true; continue; }
             mn[d] = min(mn[d], xx);
             mx[d] = max(mx[d], xx);
         }
+        typename Vec4<Real>::T p;
+        p.x = xn[0]; p.y = xn[1]; p.z = xn[2]; p.w = m[i];
+        xm[i] = p;
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_status(dstatus, TREE_DEV_NONFINITE);
     double dmn[3], dmx[3];
@@ -59,16 +68,17 @@ __global__ void __launch_bounds__(256) k_kick_drift_box(Real *__restrict__ x, Re
     }
 }
 
-cudaError_t launch_kick_drift_box(TreeWorkspace *ws, void *x, void *v, const void *a, double tau,
+cudaError_t launch_kick_drift_box(TreeWorkspace *ws, void *x, void *v, const void *a, const void *m, double tau,
                                   int64_t n, cudaStream_t s) {
-    if (ws->nseg > 1) return launch_box_segments(ws, x, v, a, tau, n, true, s);
+    if (ws->nseg > 1) return launch_box_segments(ws, x, v, a, m, tau, n, true, s);
     int nb = grid_for(n, 256, kMaxBlocksReduce);
     if (ws->p.precision == TREE_F64)
-        k_kick_drift_box<double><<<nb, 256, 0, s>>>((double *)x, (double *)v, (const double *)a, 0.5 * tau,
-                                                    tau, n, ws->part, ws->dstatus);
+        k_kick_drift_box<double><<<nb, 256, 0, s>>>((double *)x, (double *)v, (const double *)a, (const double *)m,
+                                                    (double4a *)ws->xm, 0.5 * tau, tau, n, ws->part, ws->dstatus);
     else
-        k_kick_drift_box<float><<<nb, 256, 0, s>>>((float *)x, (float *)v, (const float *)a, (float)(0.5 * tau),
-                                                   (float)tau, n, ws->part, ws->dstatus);
+        k_kick_drift_box<float><<<nb, 256, 0, s>>>((float *)x, (float *)v, (const float *)a, (const float *)m,
+                                                   (float4 *)ws->xm, (float)(0.5 * tau), (float)tau, n, ws->part,
+                                                   ws->dstatus);
     ws->launches += 1;
     return launch_box_final(ws, nb, s);
 }
