@@ -284,12 +284,19 @@ __global__ void __launch_bounds__(256) k_keys(const Real *__restrict__ x, int64_
             k = morton3(q[0], q[1], q[2]);
             key[i] = k;
         }
+        // The low five digits (the finest 13 levels) of 32 keys rarely repeat,
+        // so each lane counts its own with a shared atomic; the top three
+        // digits are aggregated over the lanes that share them first.
         const uint32_t vm = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
         for (int p = 0; p < kSortPasses; ++p) {
             const uint32_t dg = (uint32_t)((k >> (8 * p)) & 0xffu);
-            const uint32_t peers = match_digit8(dg, valid ? vm : ~vm);
-            if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&sh[p][dg], (uint32_t)__popc(peers));
+            if (p < kSortPasses - 3) {
+                if (valid) atomicAdd(&sh[p][dg], 1u);
+            } else {
+                const uint32_t peers = match_digit8(dg, valid ? vm : ~vm);
+                if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&sh[p][dg], (uint32_t)__popc(peers));
+            }
         }
     }
     __syncthreads();

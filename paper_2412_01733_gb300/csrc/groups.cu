@@ -22,19 +22,39 @@ constexpr int kGScanThreads = 256;
 constexpr int kGScanItems = 8;
 constexpr int kGScanTile = kGScanThreads * kGScanItems;
 
-// leaf level and leaf node of every sorted particle
+// Leaf level and leaf node of every sorted particle.  A warp takes 32
+// consecutive nodes and fills the particle ranges of their leaves one leaf at
+// a time, lanes over the particles (coalesced writes).
 __global__ void __launch_bounds__(256) k_leaf_levels(const uint32_t *__restrict__ ctr, const uint4 *__restrict__ ngeo,
                                                      const uint2 *__restrict__ nlink, uint8_t *__restrict__ plev,
                                                      uint32_t *__restrict__ pleaf) {
     const uint32_t nn = ctr[kCtrLevelStart + kLevels];
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nn; c += gridDim.x * blockDim.x) {
-        const uint4 g = ngeo[c];
-        if (!((g.w >> 8) & 1u)) continue;
-        const uint2 l = nlink[c];
-        const uint8_t lv = (uint8_t)(g.w & 0xffu);
-        for (uint32_t s = l.x; s < l.x + l.y; ++s) {
-            plev[s] = lv;
-            pleaf[s] = c;
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < nn; base += stride) {
+        const uint32_t c = base + lane;
+        uint32_t lv = 0, first = 0, count = 0;
+        bool leaf = false;
+        if (c < nn) {
+            const uint4 g = ngeo[c];
+            leaf = (g.w >> 8) & 1u;
+            if (leaf) {
+                const uint2 l = nlink[c];
+                lv = g.w & 0xffu;
+                first = l.x;
+                count = l.y;
+            }
+        }
+        uint32_t todo = __ballot_sync(0xffffffffu, leaf);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint32_t f = __shfl_sync(0xffffffffu, first, src), k = __shfl_sync(0xffffffffu, count, src);
+            const uint32_t l = __shfl_sync(0xffffffffu, lv, src);
+            for (uint32_t j = lane; j < k; j += 32) {
+                plev[f + j] = (uint8_t)l;
+                pleaf[f + j] = base + (uint32_t)src;
+            }
         }
     }
 }
