@@ -19,10 +19,12 @@
 //       Rbar_child += (M_child / M) Rbar + M_child (6 Qf d - 2 tr(Qf) d),
 //       Qbar_child += Qbar  (the children's quadrupoles enter Q linearly);
 //     a massless cell passes only Mbar.
-// One warp per group walks the group's stored lists.  Every staged tile of 32
-// sources is evaluated twice: lanes as targets (target cotangents, kept in
-// registers) and lanes as sources (cell / particle cotangents, added to global
-// FP64 accumulators with one atomic per quantity per source per group).
+// One warp per group walks the group's stored lists, 32 sources (cells or
+// particles) at a time, one source per lane.  Each (target, source) pair is
+// evaluated once: the source-side cotangents (cell or particle) are summed in
+// the lane and added to global FP64 accumulators with one atomic per
+// quantity per source per group; the target-side sums rotate through the
+// lanes with the targets.
 #include "common.cuh"
 
 namespace treegb {
@@ -119,12 +121,9 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_force_vjp(const AdjArgs A) {
     using V2 = typename AdjVec<Real>::V2;
     __shared__ V4 s_tp[kAdjWarps][kAdjMaxTargets];   // target position + mass
     __shared__ V4 s_tc[kAdjWarps][kAdjMaxTargets];   // target cotangent
-    __shared__ uint32_t s_ti[kAdjWarps][kAdjMaxTargets];  // target key-order index
-    __shared__ V4 s_a[kAdjWarps][32];                // staged sources: (R, M) or (x, m)
-    __shared__ Real s_q[kAdjWarps][32][6];           // staged quadrupoles
-    __shared__ uint32_t s_si[kAdjWarps][32];         // staged source index (cell or particle)
     __shared__ uint32_t s_buf[kAdjWarps][32 + 32 * kMaxLeafSmall];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int next = (lane + 1) & 31;
     const int64_t g = (int64_t)blockIdx.x * kAdjWarps + w;
     if (g >= A.ngroups) return;
     const V4 *spos = reinterpret_cast<const V4 *>(A.spos);
@@ -138,116 +137,119 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_force_vjp(const AdjArgs A) {
     for (int t = lane; t < cnt; t += 32) {
         s_tp[w][t] = spos[s0 + t];
         s_tc[w][t] = cot[s0 + t];
-        s_ti[w][t] = s0 + t;
     }
     __syncwarp();
     double xt[2][3] = {{0, 0, 0}, {0, 0, 0}};
+
+    // Every pair of a tile is evaluated once.  Lane l holds source l (a cell
+    // or a particle) and, at step k, meets target (l + k) mod 32 of the
+    // current half of the group: the source-side sums stay in the lane, the
+    // target-side partial sums travel with their target (one shuffle per step
+    // passes each to the lane that meets it next; after 32 steps a final
+    // shuffle brings target l's total to lane l).
 
     // ---- far cells ----
     const int64_t pc0 = A.list_off[g], pc1 = A.list_off[g + 1];
     for (int64_t base = pc0; base < pc1; base += 32) {
         const int nt = (int)min((int64_t)32, pc1 - base);
+        uint32_t cid = 0;
+        V4 ca{};
+        Real cq[6] = {0, 0, 0, 0, 0, 0};
         if (lane < nt) {
-            const uint32_t c = (uint32_t)A.pc_list[base + lane];
-            s_si[w][lane] = c;
-            s_a[w][lane] = momA[c];
+            cid = (uint32_t)A.pc_list[base + lane];
+            ca = momA[cid];
             if (QUAD) {
-                const V4 b = momB[c];
-                const V2 cc = momC[c];
+                const V4 b = momB[cid];
+                const V2 cc = momC[cid];
                 const Real qs = sizeof(Real) == 4 ? Real(-1) : Real(1);  // FP32 walk copies hold -Q
-                s_q[w][lane][0] = qs * b.x; s_q[w][lane][1] = qs * b.y; s_q[w][lane][2] = qs * b.z;
-                s_q[w][lane][3] = qs * b.w; s_q[w][lane][4] = qs * cc.x; s_q[w][lane][5] = qs * cc.y;
+                cq[0] = qs * b.x; cq[1] = qs * b.y; cq[2] = qs * b.z;
+                cq[3] = qs * b.w; cq[4] = qs * cc.x; cq[5] = qs * cc.y;
             }
         }
-        __syncwarp();
-        // lanes as targets
-        for (int tt = 0; tt < 2; ++tt) {
-            const int t = lane + 32 * tt;
-            if (t >= cnt) break;
-            const V4 p = s_tp[w][t];
-            const V4 b = s_tc[w][t];
-            Real ax = 0, ay = 0, az = 0;
-            for (int j = 0; j < nt; ++j) {
-                const V4 a = s_a[w][j];
-                Real q[6];
+        // the group's (at most 64) targets are summed in the working precision;
+        // the per-group totals go to the FP64 accumulators
+        Real acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
-                for (int k = 0; k < 6; ++k) q[k] = QUAD ? s_q[w][j][k] : Real(0);
-                Real gx, gy, gz, mb, qb[6];
-                pc_vjp<Real, QUAD>(p.x - a.x, p.y - a.y, p.z - a.z, b.x, b.y, b.z, b.w, a.w, q, eps2, gx, gy, gz,
-                                   mb, qb);
-                ax += gx; ay += gy; az += gz;
+        for (int h = 0; h < 2; ++h) {
+            if (32 * h >= cnt) break;
+            const int ch = min(32, cnt - 32 * h);
+            Real tx = 0, ty = 0, tz = 0;
+            for (int k = 0; k < 32; ++k) {
+                if (k > 0) {
+                    tx = __shfl_sync(0xffffffffu, tx, next);
+                    ty = __shfl_sync(0xffffffffu, ty, next);
+                    tz = __shfl_sync(0xffffffffu, tz, next);
+                }
+                const int t = (lane + k) & 31;
+                if (lane < nt && t < ch) {
+                    const V4 p = s_tp[w][32 * h + t];
+                    const V4 b = s_tc[w][32 * h + t];
+                    Real gx, gy, gz, mb, qb[6];
+                    pc_vjp<Real, QUAD>(p.x - ca.x, p.y - ca.y, p.z - ca.z, b.x, b.y, b.z, b.w, ca.w, cq, eps2, gx,
+                                       gy, gz, mb, qb);
+                    tx += gx; ty += gy; tz += gz;
+                    acc[0] += mb;
+                    acc[1] -= gx; acc[2] -= gy; acc[3] -= gz;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) acc[4 + q] += qb[q];
+                }
             }
-            xt[tt][0] += (double)ax; xt[tt][1] += (double)ay; xt[tt][2] += (double)az;
+            tx = __shfl_sync(0xffffffffu, tx, next);
+            ty = __shfl_sync(0xffffffffu, ty, next);
+            tz = __shfl_sync(0xffffffffu, tz, next);
+            if (lane < ch) { xt[h][0] += (double)tx; xt[h][1] += (double)ty; xt[h][2] += (double)tz; }
         }
-        // lanes as cells
         if (lane < nt) {
-            const V4 a = s_a[w][lane];
-            Real q[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) q[k] = QUAD ? s_q[w][lane][k] : Real(0);
-            // the group's (at most 64) targets are summed in the working precision;
-            // the per-group totals go to the FP64 accumulators
-            Real acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-            for (int t = 0; t < cnt; ++t) {
-                const V4 p = s_tp[w][t];
-                const V4 b = s_tc[w][t];
-                Real gx, gy, gz, mb, qb[6];
-                pc_vjp<Real, QUAD>(p.x - a.x, p.y - a.y, p.z - a.z, b.x, b.y, b.z, b.w, a.w, q, eps2, gx, gy, gz,
-                                   mb, qb);
-                acc[0] += mb;
-                acc[1] -= gx; acc[2] -= gy; acc[3] -= gz;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) acc[4 + k] += qb[k];
-            }
-            const uint32_t c = s_si[w][lane];
-#pragma unroll
-            for (int k = 0; k < (QUAD ? 10 : 4); ++k)
-                if (acc[k] != Real(0)) atomicAdd(A.ccot + (int64_t)k * A.cap + c, A.G * (double)acc[k]);
+            for (int q = 0; q < (QUAD ? 10 : 4); ++q)
+                if (acc[q] != Real(0)) atomicAdd(A.ccot + (int64_t)q * A.cap + cid, A.G * (double)acc[q]);
         }
-        __syncwarp();
     }
 
     // ---- near leaves: expand particles into the buffer, tiles of 32 ----
     const int64_t pp0 = A.list_off[A.ngroups + 1 + g], pp1 = A.list_off[A.ngroups + 1 + g + 1];
     auto pp_tile = [&](const uint32_t *src, int nt) {
+        uint32_t sj = 0;
+        V4 sa{};
         if (lane < nt) {
-            const uint32_t j = src[lane];
-            s_si[w][lane] = j;
-            s_a[w][lane] = spos[j];
+            sj = src[lane];
+            sa = spos[sj];
         }
         __syncwarp();
-        for (int tt = 0; tt < 2; ++tt) {
-            const int t = lane + 32 * tt;
-            if (t >= cnt) break;
-            const V4 p = s_tp[w][t];
-            const V4 b = s_tc[w][t];
-            const uint32_t ti = s_ti[w][t];
-            Real ax = 0, ay = 0, az = 0;
-            for (int k = 0; k < nt; ++k) {
-                if (s_si[w][k] == ti) continue;
-                const V4 a = s_a[w][k];
-                Real gx, gy, gz, dm;
-                pp_vjp<Real>(a.x - p.x, a.y - p.y, a.z - p.z, b.x, b.y, b.z, b.w, a.w, eps2, gx, gy, gz, dm);
-                ax -= gx; ay -= gy; az -= gz;
+        Real gxs = 0, gys = 0, gzs = 0, dms = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (32 * h >= cnt) break;
+            const int ch = min(32, cnt - 32 * h);
+            Real tx = 0, ty = 0, tz = 0;
+            for (int k = 0; k < 32; ++k) {
+                if (k > 0) {
+                    tx = __shfl_sync(0xffffffffu, tx, next);
+                    ty = __shfl_sync(0xffffffffu, ty, next);
+                    tz = __shfl_sync(0xffffffffu, tz, next);
+                }
+                const int t = (lane + k) & 31;
+                // the self pair is excluded by index
+                if (lane < nt && t < ch && s0 + (uint32_t)(32 * h + t) != sj) {
+                    const V4 p = s_tp[w][32 * h + t];
+                    const V4 b = s_tc[w][32 * h + t];
+                    Real gx, gy, gz, dm;
+                    pp_vjp<Real>(sa.x - p.x, sa.y - p.y, sa.z - p.z, b.x, b.y, b.z, b.w, sa.w, eps2, gx, gy, gz,
+                                 dm);
+                    tx -= gx; ty -= gy; tz -= gz;
+                    gxs += gx; gys += gy; gzs += gz; dms += dm;
+                }
             }
-            xt[tt][0] += (double)ax; xt[tt][1] += (double)ay; xt[tt][2] += (double)az;
+            tx = __shfl_sync(0xffffffffu, tx, next);
+            ty = __shfl_sync(0xffffffffu, ty, next);
+            tz = __shfl_sync(0xffffffffu, tz, next);
+            if (lane < ch) { xt[h][0] += (double)tx; xt[h][1] += (double)ty; xt[h][2] += (double)tz; }
         }
         if (lane < nt) {
-            const V4 a = s_a[w][lane];
-            const uint32_t j = s_si[w][lane];
-            Real gxs = 0, gys = 0, gzs = 0, dms = 0;
-            for (int t = 0; t < cnt; ++t) {
-                if (s_ti[w][t] == j) continue;
-                const V4 p = s_tp[w][t];
-                const V4 b = s_tc[w][t];
-                Real gx, gy, gz, dm;
-                pp_vjp<Real>(a.x - p.x, a.y - p.y, a.z - p.z, b.x, b.y, b.z, b.w, a.w, eps2, gx, gy, gz, dm);
-                gxs += gx; gys += gy; gzs += gz; dms += dm;
-            }
-            atomicAdd(A.xg + j, A.G * (double)gxs);
-            atomicAdd(A.xg + A.n + j, A.G * (double)gys);
-            atomicAdd(A.xg + 2 * A.n + j, A.G * (double)gzs);
-            atomicAdd(A.mg + j, A.G * (double)dms);
+            atomicAdd(A.xg + sj, A.G * (double)gxs);
+            atomicAdd(A.xg + A.n + sj, A.G * (double)gys);
+            atomicAdd(A.xg + 2 * A.n + sj, A.G * (double)gzs);
+            atomicAdd(A.mg + sj, A.G * (double)dms);
         }
         __syncwarp();
     };
