@@ -340,6 +340,28 @@ def test_leapfrog_plain_config(orc):
     np.testing.assert_allclose(d1[5:8], do["L"], atol=1e-5)
 
 
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_leapfrog_forces_equal_standalone_evaluation(precision):
+    """The leapfrog's force pass reads the packed (x, y, z, m) copy written by its
+    kick-drift pass; a separate tree_build + tree_moments + tree_forces on the
+    drifted positions reads the caller's arrays.  Same tree, same sums: the
+    accelerations and potentials must agree bit for bit."""
+    tg = _tg()
+    n, tau = 20011, 0.005
+    x, v, m = inputs.galaxy(n, 7)
+    dt = torch.float64 if precision == "f64" else torch.float32
+    xg, vg, mg = (t.to("cuda", dt).contiguous() for t in (x, v, m))
+    p = dict(eps=0.02, theta=0.6, order=2, leaf_cap=16, group_size=32, precision=precision)
+    with tg.Workspace(n, **p) as ws, tg.Workspace(n, **p) as w2:
+        a, phi = ws.accel(xg, mg)
+        ws.leapfrog_step(xg, vg, mg, a, tau, phi=phi)
+        a2, phi2 = w2.accel(xg, mg)
+        torch.cuda.synchronize()
+        assert ws.status() == 0 and w2.status() == 0
+        assert torch.equal(a, a2)
+        assert torch.equal(phi, phi2)
+
+
 def test_diagnostics_match_oracle(orc):
     tg = _tg()
     x, v, m = inputs.plummer(5000, 2)
