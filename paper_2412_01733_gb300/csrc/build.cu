@@ -218,7 +218,7 @@ cudaError_t launch_box_segments(TreeWorkspace *ws, void *x, void *v, const void 
 
 template <typename Real>
 static cudaError_t box_impl(TreeWorkspace *ws, const Real *x, int64_t n, cudaStream_t s) {
-    int nb = grid_for(n, 256, kMaxBlocksReduce);
+    const int nb = wave_grid(k_box_partial<Real>, n, 256, kMaxBlocksReduce);
     k_box_partial<Real><<<nb, 256, 0, s>>>(x, n, ws->part, ws->dstatus);
     ws->launches += 1;
     return launch_box_final(ws, nb, s);
@@ -468,12 +468,13 @@ static bool sort_starts_alt(const TreeWorkspace *ws) { return ((kSortPasses + ws
 
 template <typename Real>
 static cudaError_t keys_impl(TreeWorkspace *ws, const Real *x, int64_t n, cudaStream_t s) {
-    int nb = grid_for(n, 256, 152 * 8);
     uint64_t *dst = sort_starts_alt(ws) ? ws->key_alt : ws->key;
     if (ws->nseg > 1)
-        k_keys<Real, true><<<nb, 256, 0, s>>>(x, n, ws->box, ws->seg_off, ws->nseg, dst, ws->hist);
+        k_keys<Real, true><<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(
+            x, n, ws->box, ws->seg_off, ws->nseg, dst, ws->hist);
     else
-        k_keys<Real, false><<<nb, 256, 0, s>>>(x, n, ws->box, nullptr, 1, dst, ws->hist);
+        k_keys<Real, false><<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(
+            x, n, ws->box, nullptr, 1, dst, ws->hist);
     k_hist_scan<<<kSortPasses, kRadix, 0, s>>>(ws->hist);
     ws->launches += 2;
     return cudaGetLastError();

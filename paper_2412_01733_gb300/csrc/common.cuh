@@ -315,6 +315,23 @@ inline int grid_for(int64_t n, int threads, int max_blocks) {
     return (int)b;
 }
 
+// Grid of a grid-stride kernel: grid_for, cut to one wave of the blocks that
+// fit on the device at once.  Every block of a grid-stride loop carries the
+// same share of the work, so a partial last wave would take as long as a
+// full one (e.g. 1024 blocks at 3 resident per SM: three waves for 2.25
+// waves of work).
+template <typename Kernel>
+inline int wave_grid(Kernel k, int64_t n, int threads, int max_blocks, size_t smem = 0) {
+    int nb = grid_for(n, threads, max_blocks);
+    int dev = 0, per_sm = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) == cudaSuccess && per_sm > 0 &&
+        (int64_t)per_sm * sms < nb)
+        nb = per_sm * sms;
+    return nb;
+}
+
 }  // namespace treegb
 
 // ---------------------------------------------------------------- host-side entry points of each .cu

@@ -71,14 +71,17 @@ __global__ void __launch_bounds__(256) k_kick_drift_box(Real *__restrict__ x, Re
 cudaError_t launch_kick_drift_box(TreeWorkspace *ws, void *x, void *v, const void *a, const void *m, double tau,
                                   int64_t n, cudaStream_t s) {
     if (ws->nseg > 1) return launch_box_segments(ws, x, v, a, m, tau, n, true, s);
-    int nb = grid_for(n, 256, kMaxBlocksReduce);
-    if (ws->p.precision == TREE_F64)
+    int nb;
+    if (ws->p.precision == TREE_F64) {
+        nb = wave_grid(k_kick_drift_box<double>, n, 256, kMaxBlocksReduce);
         k_kick_drift_box<double><<<nb, 256, 0, s>>>((double *)x, (double *)v, (const double *)a, (const double *)m,
                                                     (double4a *)ws->xm, 0.5 * tau, tau, n, ws->part, ws->dstatus);
-    else
+    } else {
+        nb = wave_grid(k_kick_drift_box<float>, n, 256, kMaxBlocksReduce);
         k_kick_drift_box<float><<<nb, 256, 0, s>>>((float *)x, (float *)v, (const float *)a, (const float *)m,
                                                    (float4 *)ws->xm, (float)(0.5 * tau), (float)tau, n, ws->part,
                                                    ws->dstatus);
+    }
     ws->launches += 1;
     return launch_box_final(ws, nb, s);
 }
@@ -154,7 +157,8 @@ __global__ void __launch_bounds__(256) k_diag_final(const double *__restrict__ p
 
 cudaError_t launch_diagnostics(TreeWorkspace *ws, const void *x, const void *v, const void *m,
                                const void *phi, int64_t n, double *out, cudaStream_t s) {
-    int nb = grid_for(n, 256, kMaxBlocksReduce);
+    const int nb = ws->p.precision == TREE_F64 ? wave_grid(k_diag_partial<double>, n, 256, kMaxBlocksReduce)
+                                               : wave_grid(k_diag_partial<float>, n, 256, kMaxBlocksReduce);
     if (ws->p.precision == TREE_F64)
         k_diag_partial<double><<<nb, 256, 0, s>>>((const double *)x, (const double *)v, (const double *)m,
                                                   (const double *)phi, n, ws->part);

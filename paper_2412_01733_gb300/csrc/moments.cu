@@ -210,14 +210,16 @@ static cudaError_t moments_impl(TreeWorkspace *ws, cudaStream_t s) {
     uint32_t *cnt = ws->mbucket, *off = ws->mbucket + kMomBuckets, *cursor = ws->mbucket + 2 * kMomBuckets + 1;
     cudaError_t e = cudaMemsetAsync(ws->mbucket, 0, (3 * kMomBuckets + 1) * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    const int nb = grid_for(ws->node_cap, 256, 152 * 8);
-    k_mom_hist<<<nb, 256, 0, s>>>(ws->ctr, ws->ngeo, ws->nlink, cnt);
-    k_mom_scatter<<<nb, 256, 0, s>>>(ws->ctr, ws->ngeo, ws->nlink, cnt, off, cursor, ws->morder);
-    k_moments_leaves<Real><<<nb, 256, 0, s>>>(off, ws->morder, ws->ngeo, ws->nlink, (const V4 *)ws->spos, ws->box,
-                                              ws->nfirst, ws->seg_off, ws->nseg, ws->mom64, ws->node_cap,
-                                              (V4 *)ws->mom_a, (V4 *)ws->mom_b, (V2 *)ws->mom_c);
+    const int64_t cap = ws->node_cap;
+    k_mom_hist<<<grid_for(cap, 256, 152 * 8), 256, 0, s>>>(ws->ctr, ws->ngeo, ws->nlink, cnt);
+    k_mom_scatter<<<grid_for(cap, 256, 152 * 8), 256, 0, s>>>(ws->ctr, ws->ngeo, ws->nlink, cnt, off,
+                                                                             cursor, ws->morder);
+    k_moments_leaves<Real><<<grid_for(cap, 256, 152 * 8), 256, 0, s>>>(
+        off, ws->morder, ws->ngeo, ws->nlink, (const V4 *)ws->spos, ws->box, ws->nfirst, ws->seg_off, ws->nseg,
+        ws->mom64, cap, (V4 *)ws->mom_a, (V4 *)ws->mom_b, (V2 *)ws->mom_c);
+    const int nbl = grid_for(cap, 256, 152 * 8);
     for (int L = kMaxLevel - 1; L >= 0; --L)
-        k_moments_level<Real><<<nb, 256, 0, s>>>(L, off, ws->morder, ws->ngeo, ws->nlink, ws->box, ws->nfirst,
+        k_moments_level<Real><<<nbl, 256, 0, s>>>(L, off, ws->morder, ws->ngeo, ws->nlink, ws->box, ws->nfirst,
                                                  ws->seg_off, ws->nseg, ws->mom64, ws->node_cap, (V4 *)ws->mom_a,
                                                  (V4 *)ws->mom_b, (V2 *)ws->mom_c);
     ws->launches += 3 + kMaxLevel;
