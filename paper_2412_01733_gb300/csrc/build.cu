@@ -415,24 +415,7 @@ __global__ void __launch_bounds__(kSortThreads, MODE == kPassSeg ? 2 : 3) k_ones
             st_release(st, kFlagInc | tcount);
         } else {
             st_release(st + (size_t)tile * kRadix, kFlagAgg | tcount);
-            int64_t p = (int64_t)tile - 1;
-            while (p >= 0) {
-                uint32_t w = ld_acquire(st + (size_t)p * kRadix);
-                if ((w & ~kValMask) == 0) {
-                    long long t0 = clock64();
-                    while (((w = ld_acquire(st + (size_t)p * kRadix)) & ~kValMask) == 0) {
-                        if (clock64() - t0 > kWaitCycles) {
-                            set_status(dstatus, TREE_DEV_TIMEOUT);
-                            w = kFlagInc;
-                            break;
-                        }
-                        __nanosleep(32);
-                    }
-                }
-                excl += w & kValMask;
-                if ((w & ~kValMask) == kFlagInc) break;
-                --p;
-            }
+            excl = lookback_walk(st, kRadix, (int64_t)tile - 1, dstatus);
             st_release(st + (size_t)tile * kRadix, kFlagInc | ((excl + tcount) & kValMask));
         }
         S.gbase[d] = digit_off[d] + excl;

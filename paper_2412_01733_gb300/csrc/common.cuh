@@ -177,11 +177,6 @@ struct TreeWorkspace {
 namespace treegb {
 
 // ---------------------------------------------------------------- device helpers
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -237,6 +232,47 @@ __device__ __forceinline__ void set_status(int32_t *st, int32_t bits) {
 // `tile` given its aggregate.  Call from one thread.  A wait that exceeds
 // kWaitCycles sets TREE_DEV_TIMEOUT and ends the look-back (the published
 // inclusive value is then wrong, but every waiter terminates).
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Exclusive prefix of the tile after tile p from the look-back words of tiles
+// p, p-1, ... (word of tile q at st[q * stride]): adds aggregates back to the
+// first inclusive prefix.  Four predecessors are read at a time (independent
+// loads; flag and value share one word, so relaxed loads suffice), so a walk
+// over k tiles costs about k/4 load latencies; a word not yet published is
+// waited for (bounded: past kWaitCycles it sets TREE_DEV_TIMEOUT and ends the
+// walk).
+__device__ inline uint32_t lookback_walk(const uint32_t *st, size_t stride, int64_t p, int32_t *dstatus) {
+    uint32_t excl = 0;
+    while (p >= 0) {
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) w[j] = p - j >= 0 ? ld_relaxed(st + (size_t)(p - j) * stride) : kFlagInc;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint32_t v = w[j];
+            if ((v & ~kValMask) == 0) {
+                long long t0 = clock64();
+                while (((v = ld_relaxed(st + (size_t)(p - j) * stride)) & ~kValMask) == 0) {
+                    if (clock64() - t0 > kWaitCycles) {
+                        set_status(dstatus, TREE_DEV_TIMEOUT);
+                        v = kFlagInc;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            excl += v & kValMask;
+            if ((v & ~kValMask) == kFlagInc) return excl;
+        }
+        p -= 4;
+    }
+    return excl;
+}
+
 __device__ inline uint32_t lookback_single(uint32_t *status, uint32_t tile, uint32_t agg,
                                            int32_t *dstatus) {
     if (tile == 0) {
@@ -244,25 +280,7 @@ __device__ inline uint32_t lookback_single(uint32_t *status, uint32_t tile, uint
         return 0;
     }
     st_release(status + tile, kFlagAgg | (agg & kValMask));
-    uint32_t excl = 0;
-    int64_t p = (int64_t)tile - 1;
-    while (p >= 0) {
-        uint32_t v = ld_acquire(status + p);
-        if ((v & ~kValMask) == 0) {
-            long long t0 = clock64();
-            while (((v = ld_acquire(status + p)) & ~kValMask) == 0) {
-                if (clock64() - t0 > kWaitCycles) {
-                    set_status(dstatus, TREE_DEV_TIMEOUT);
-                    v = kFlagInc;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        excl += v & kValMask;
-        if ((v & ~kValMask) == kFlagInc) break;
-        --p;
-    }
+    const uint32_t excl = lookback_walk(status, 1, (int64_t)tile - 1, dstatus);
     st_release(status + tile, kFlagInc | ((excl + agg) & kValMask));
     return excl;
 }
