@@ -17,7 +17,7 @@ namespace treegb {
 // in caller order, from which the tree's gather reads one aligned vector per
 // particle instead of four scattered scalars.
 template <typename Real>
-__global__ void __launch_bounds__(256) k_kick_drift_box(Real *__restrict__ x, Real *__restrict__ v,
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 6 : 3) k_kick_drift_box(Real *__restrict__ x, Real *__restrict__ v,
                                                         const Real *__restrict__ a, const Real *__restrict__ m,
                                                         typename Vec4<Real>::T *__restrict__ xm, Real half_tau,
                                                         Real tau, int64_t n, double *__restrict__ part,
