@@ -228,10 +228,6 @@ __device__ __forceinline__ void set_status(int32_t *st, int32_t bits) {
     atomicOr(st, bits);
 }
 
-// Single-value decoupled look-back: returns the exclusive prefix of tile
-// `tile` given its aggregate.  Call from one thread.  A wait that exceeds
-// kWaitCycles sets TREE_DEV_TIMEOUT and ends the look-back (the published
-// inclusive value is then wrong, but every waiter terminates).
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -273,6 +269,10 @@ __device__ inline uint32_t lookback_walk(const uint32_t *st, size_t stride, int6
     return excl;
 }
 
+// Single-value decoupled look-back: returns the exclusive prefix of tile
+// `tile` given its aggregate.  Call from one thread.  A wait that exceeds
+// kWaitCycles sets TREE_DEV_TIMEOUT and ends the look-back (the published
+// inclusive value is then wrong, but every waiter terminates).
 __device__ inline uint32_t lookback_single(uint32_t *status, uint32_t tile, uint32_t agg,
                                            int32_t *dstatus) {
     if (tile == 0) {
