@@ -645,6 +645,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
         }
     }
     if (MODE == kWalkForce) {
+        // every traversal step evaluates the whole tiles, so fewer than 32
+        // entries are left here: the staging holds at most 32 sources
         if (npc > 0) eval_pc_list(pcbuf, npc);
         if (npp > 0) eval_pp_list(ppbuf, npp);
     }
