@@ -101,6 +101,7 @@ void orc_keys(int64_t n, const double *x, const double *lo, int32_t k,
 {
     const double scale = ldexp(1.0, ORC_BITS - k);
     const double qmax = (double)((1u << ORC_BITS) - 1u);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         uint32_t qq[3];
         for (int d = 0; d < 3; ++d) {
@@ -276,17 +277,35 @@ void orc_moments(int64_t nn, const int64_t *first, const int64_t *count,
  * P = number of leading octal digits the two keys share (21 if equal), and
  * where the cell of level P holding both (their smallest common cell) has more
  * than cmax particles.  delta = 0 disables the first cut, cmax = 0 the second.
+ * The population of that cell is the number of sorted keys whose first P
+ * octal digits equal key i's: keys are sorted, so they form one run, whose
+ * ends two binary searches over (key >> 3(21 - P)) find.
  * gfirst (capacity n + 1) receives the first sorted index of every group and n
  * at the end; returns the group count. */
+static int64_t orc_prefix_bound(int64_t n, const uint64_t *skey, int sh, uint64_t pre, int upper)
+{
+    /* first j with (skey[j] >> sh) > pre (upper) or >= pre (lower) */
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        uint64_t v = sh >= 64 ? 0 : skey[mid] >> sh;
+        int go_right = upper ? (v <= pre) : (v < pre);
+        if (go_right) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 int64_t orc_groups(int64_t n, const uint64_t *skey, int64_t nn, const int32_t *level, const int64_t *first,
                    const int64_t *count, const int32_t *nchild, int32_t gs, int32_t delta, int64_t cmax,
                    int64_t *gfirst)
 {
     int32_t *lv = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    unsigned char *cut = (unsigned char *)malloc((size_t)(n > 0 ? n : 1));
     for (int64_t c = 0; c < nn; ++c)
         if (nchild[c] == 0)
             for (int64_t s = first[c]; s < first[c] + count[c]; ++s) lv[s] = level[c];
-    int64_t ng = 0;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         int start = (i % gs) == 0;
         if (!start && (delta > 0 || cmax > 0)) {
@@ -299,24 +318,19 @@ int64_t orc_groups(int64_t n, const uint64_t *skey, int64_t nn, const int32_t *l
             int lmax = lv[i - 1] > lv[i] ? lv[i - 1] : lv[i];
             if (delta > 0 && common < lmax - delta) start = 1;
             if (!start && cmax > 0) {
-                /* particles whose keys share the first `common` digits with key i */
                 const int sh = 3 * (21 - common);
                 const uint64_t pre = sh >= 64 ? 0 : skey[i] >> sh;
-                int64_t cnt = 1;
-                for (int64_t j = i - 1; j >= 0 && cnt <= cmax; --j) {
-                    if ((sh >= 64 ? 0 : skey[j] >> sh) != pre) break;
-                    ++cnt;
-                }
-                for (int64_t j = i + 1; j < n && cnt <= cmax; ++j) {
-                    if ((sh >= 64 ? 0 : skey[j] >> sh) != pre) break;
-                    ++cnt;
-                }
+                const int64_t cnt = orc_prefix_bound(n, skey, sh, pre, 1) - orc_prefix_bound(n, skey, sh, pre, 0);
                 if (cnt > cmax) start = 1;
             }
         }
-        if (start) gfirst[ng++] = i;
+        cut[i] = (unsigned char)start;
     }
+    int64_t ng = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (cut[i]) gfirst[ng++] = i;
     gfirst[ng] = n;
+    free(cut);
     free(lv);
     return ng;
 }
@@ -332,56 +346,93 @@ int64_t orc_groups(int64_t n, const uint64_t *skey, int64_t nn, const int32_t *l
  *   the children.  The walk is breadth first in node order, so both lists
  *   come out in ascending node index.
  * qs: (3, n) quantised coordinates in SORTED order.
- * Call once with pc_list = pp_list = NULL to get the offsets (CSR, ngroups+1
- * entries each), then again with lists of the sizes pc_off[ng], pp_off[ng]. */
-void orc_lists(int64_t n, const uint32_t *qs, int64_t ng, const int64_t *gfirst, double theta,
+ * gsel (nsel entries, or NULL for all ng groups in order): the groups to walk;
+ * entry k of the CSR output belongs to group gsel[k].
+ * Call once with pc_list = pp_list = NULL to get the offsets (CSR, nsel+1
+ * entries each), then again with lists of the sizes pc_off[nsel], pp_off[nsel].
+ * Each group's walk is independent of the others (OpenMP over groups).
+ *
+ * orc_walk_group: one group's walk; writes its lists at pc/pp when they are
+ * non-NULL and returns the two list lengths.  queue: scratch of nn entries. */
+static void orc_walk_group(const uint32_t *qs, int64_t n, int64_t s0, int64_t s1, double th2, int64_t nn,
+                           const int32_t *level, const uint32_t *corner, const int64_t *child,
+                           const int32_t *nchild, int64_t *queue, int64_t *pc, int64_t *pp,
+                           int64_t *npc_out, int64_t *npp_out)
+{
+    int64_t glo[3], ghi[3];
+    for (int d = 0; d < 3; ++d) {
+        uint32_t mn = qs[d * n + s0], mx = qs[d * n + s0];
+        for (int64_t s = s0; s < s1; ++s) {
+            uint32_t v = qs[d * n + s];
+            if (v < mn) mn = v;
+            if (v > mx) mx = v;
+        }
+        glo[d] = mn; ghi[d] = (int64_t)mx + 1;
+    }
+    int64_t npc = 0, npp = 0, head = 0, tail = 0;
+    if (nn > 0) queue[tail++] = 0;
+    while (head < tail) {
+        int64_t c = queue[head++];
+        int64_t sd = (int64_t)1 << (ORC_BITS - level[c]);
+        int64_t d2 = 0;
+        for (int d = 0; d < 3; ++d) {
+            int64_t cd = corner[d * nn + c];
+            int64_t gap = 0;
+            if (cd - ghi[d] > gap) gap = cd - ghi[d];
+            if (glo[d] - (cd + sd) > gap) gap = glo[d] - (cd + sd);
+            d2 += gap * gap;
+        }
+        int accept = (double)(sd * sd) < th2 * (double)d2;
+        if (accept) {
+            if (pc) pc[npc] = c;
+            ++npc;
+        } else if (nchild[c] == 0) {
+            if (pp) pp[npp] = c;
+            ++npp;
+        } else {
+            for (int32_t k = 0; k < nchild[c]; ++k) queue[tail++] = child[c] + k;
+        }
+    }
+    *npc_out = npc; *npp_out = npp;
+}
+
+void orc_lists(int64_t n, const uint32_t *qs, int64_t ng, const int64_t *gfirst, int64_t nsel,
+               const int64_t *gsel, double theta,
                int64_t nn, const int32_t *level, const uint32_t *corner /* (3, nn) */,
                const int64_t *child, const int32_t *nchild,
                int64_t *pc_off, int64_t *pp_off, int64_t *pc_list, int64_t *pp_list)
 {
     const double th2 = theta * theta;
-    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nn > 0 ? nn : 1));
-    int64_t npc = 0, npp = 0;
-    for (int64_t g = 0; g < ng; ++g) {
-        pc_off[g] = npc; pp_off[g] = npp;
-        int64_t s0 = gfirst[g], s1 = gfirst[g + 1];
-        int64_t glo[3], ghi[3];
-        for (int d = 0; d < 3; ++d) {
-            uint32_t mn = qs[d * n + s0], mx = qs[d * n + s0];
-            for (int64_t s = s0; s < s1; ++s) {
-                uint32_t v = qs[d * n + s];
-                if (v < mn) mn = v;
-                if (v > mx) mx = v;
-            }
-            glo[d] = mn; ghi[d] = (int64_t)mx + 1;
+    if (!gsel) nsel = ng;
+    /* the groups' walks are independent: lengths first, then offsets, then (second call) the lists */
+#pragma omp parallel
+    {
+        int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nn > 0 ? nn : 1));
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t k = 0; k < nsel; ++k) {
+            const int64_t g = gsel ? gsel[k] : k;
+            int64_t a, b;
+            orc_walk_group(qs, n, gfirst[g], gfirst[g + 1], th2, nn, level, corner, child, nchild, queue,
+                           NULL, NULL, &a, &b);
+            pc_off[k + 1] = a; pp_off[k + 1] = b;
         }
-        int64_t head = 0, tail = 0;
-        if (nn > 0) queue[tail++] = 0;
-        while (head < tail) {
-            int64_t c = queue[head++];
-            int64_t sd = (int64_t)1 << (ORC_BITS - level[c]);
-            int64_t d2 = 0;
-            for (int d = 0; d < 3; ++d) {
-                int64_t cd = corner[d * nn + c];
-                int64_t gap = 0;
-                if (cd - ghi[d] > gap) gap = cd - ghi[d];
-                if (glo[d] - (cd + sd) > gap) gap = glo[d] - (cd + sd);
-                d2 += gap * gap;
-            }
-            int accept = (double)(sd * sd) < th2 * (double)d2;
-            if (accept) {
-                if (pc_list) pc_list[npc] = c;
-                ++npc;
-            } else if (nchild[c] == 0) {
-                if (pp_list) pp_list[npp] = c;
-                ++npp;
-            } else {
-                for (int32_t k = 0; k < nchild[c]; ++k) queue[tail++] = child[c] + k;
-            }
-        }
+        free(queue);
     }
-    pc_off[ng] = npc; pp_off[ng] = npp;
-    free(queue);
+    pc_off[0] = 0; pp_off[0] = 0;
+    for (int64_t k = 0; k < nsel; ++k) { pc_off[k + 1] += pc_off[k]; pp_off[k + 1] += pp_off[k]; }
+    if (!pc_list || !pp_list) return;
+#pragma omp parallel
+    {
+        int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nn > 0 ? nn : 1));
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t k = 0; k < nsel; ++k) {
+            const int64_t g = gsel ? gsel[k] : k;
+            int64_t a, b;
+            orc_walk_group(qs, n, gfirst[g], gfirst[g + 1], th2, nn, level, corner, child, nchild, queue,
+                           pc_list + pc_off[k], pp_list + pp_off[k], &a, &b);
+        }
+        free(queue);
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -390,23 +441,29 @@ void orc_lists(int64_t n, const uint32_t *qs, int64_t ng, const int64_t *gfirst,
  *   a   = -G M y / r_s^3 + G (Q y) / r_s^5 - (5/2) G (y^T Q y) y / r_s^7
  *   phi = -G M / r_s - (1/2) G (y^T Q y) / r_s^5
  * (monopole: Q = 0).  PP part: Eq. 1 over the members of each near leaf,
- * j != i.  x, m in original order; outputs in original order. */
+ * j != i.  x, m in original order; outputs in original order.  gsel (nsel
+ * entries, or NULL for all ng groups): the groups evaluated, with their lists
+ * at CSR entry k as orc_lists gives them; other particles' outputs are left
+ * as they are. */
 void orc_tree_forces(int64_t n, const double *x, const double *m, const int64_t *perm,
-                     int64_t ng, const int64_t *gfirst, int64_t nn, const double *M, const double *R, const double *Q,
+                     int64_t ng, const int64_t *gfirst, int64_t nsel, const int64_t *gsel,
+                     int64_t nn, const double *M, const double *R, const double *Q,
                      const int64_t *first, const int64_t *count,
                      const int64_t *pc_off, const int64_t *pc_list,
                      const int64_t *pp_off, const int64_t *pp_list,
                      double G, double eps, int32_t quad, double *a, double *phi)
 {
     const double eps2 = eps * eps;
+    if (!gsel) nsel = ng;
 #pragma omp parallel for schedule(dynamic, 4)
-    for (int64_t g = 0; g < ng; ++g) {
+    for (int64_t kk = 0; kk < nsel; ++kk) {
+        const int64_t g = gsel ? gsel[kk] : kk;
         int64_t s0 = gfirst[g], s1 = gfirst[g + 1];
         for (int64_t s = s0; s < s1; ++s) {
             int64_t i = perm[s];
             double xi = x[i], yi = x[n + i], zi = x[2 * n + i];
             double ax = 0.0, ay = 0.0, az = 0.0, p = 0.0;
-            for (int64_t e = pc_off[g]; e < pc_off[g + 1]; ++e) {
+            for (int64_t e = pc_off[kk]; e < pc_off[kk + 1]; ++e) {
                 int64_t c = pc_list[e];
                 double yx = xi - R[c], yy = yi - R[nn + c], yz = zi - R[2 * nn + c];
                 double r2 = yx * yx + yy * yy + yz * yz + eps2;
@@ -430,7 +487,7 @@ void orc_tree_forces(int64_t n, const double *x, const double *m, const int64_t 
                     p -= 0.5 * G * yQy * i5;
                 }
             }
-            for (int64_t e = pp_off[g]; e < pp_off[g + 1]; ++e) {
+            for (int64_t e = pp_off[kk]; e < pp_off[kk + 1]; ++e) {
                 int64_t c = pp_list[e];
                 for (int64_t t = first[c]; t < first[c] + count[c]; ++t) {
                     int64_t j = perm[t];

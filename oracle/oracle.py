@@ -45,9 +45,9 @@ def lib():
         L.orc_moments.argtypes = [i64, _I64, _I64, _D, _I64, i64, _D, _D, _D, _D, _D]
         L.orc_groups.argtypes = [i64, _U64, i64, _I32, _I64, _I64, _I32, i32, i32, i64, _I64]
         L.orc_groups.restype = i64
-        L.orc_lists.argtypes = [i64, _U32, i64, _I64, dbl, i64, _I32, _U32, _I64, _I32,
+        L.orc_lists.argtypes = [i64, _U32, i64, _I64, i64, _I64, dbl, i64, _I32, _U32, _I64, _I32,
                                 _I64, _I64, _I64, _I64]
-        L.orc_tree_forces.argtypes = [i64, _D, _D, _I64, i64, _I64, i64, _D, _D, _D, _I64, _I64,
+        L.orc_tree_forces.argtypes = [i64, _D, _D, _I64, i64, _I64, i64, _I64, i64, _D, _D, _D, _I64, _I64,
                                       _I64, _I64, _I64, _I64, dbl, dbl, i32, _D, _D]
         L.orc_tree_forces_vjp.argtypes = [i64, _D, _D, _I64, i64, _I64, i64, _D, _D, _D, _I64, _I64,
                                           _I64, _I64, _I64, _I64, dbl, dbl, i32, _D, _D, _D, _D]
@@ -136,7 +136,7 @@ class Octree:
 def octree(skey, lcap):
     skey = np.ascontiguousarray(skey, dtype=np.uint64)
     n = skey.shape[0]
-    cap = max(64, 2 * n)
+    cap = 0 if n > (1 << 22) else max(64, 2 * n)   # large n: count first, then fill exact arrays
     while True:
         lv = np.zeros(cap, np.int32); co = np.zeros((3, cap), np.uint32)
         fi = np.zeros(cap, np.int64); cn = np.zeros(cap, np.int64)
@@ -157,13 +157,18 @@ def cell_centre(tree: Octree, lo, k):
 
 
 def moments(tree: Octree, perm, x, m, lo, k):
+    """Cell moments (orc_moments).  The members of a cell are sorted positions first..first+count,
+    i.e. particles perm[first..]; they are passed in sorted order (the same particles, summed in the
+    same order) so the sums read memory contiguously."""
     x = _f64(x); m = _f64(m)
     nn = tree.nn
     cen = np.ascontiguousarray(cell_centre(tree, lo, k))
     M = np.zeros(nn); R = np.zeros((3, nn)); Q = np.zeros((6, nn))
     perm = np.ascontiguousarray(perm, dtype=np.int64)
+    xs = np.ascontiguousarray(x[:, perm]); ms = np.ascontiguousarray(m[perm])
+    ident = np.arange(perm.shape[0], dtype=np.int64)
     lib().orc_moments(nn, _p(tree.first, _I64), _p(tree.count, _I64), _p(cen, _D),
-                      _p(perm, _I64), m.shape[0], _p(x, _D), _p(m, _D),
+                      _p(ident, _I64), ms.shape[0], _p(xs, _D), _p(ms, _D),
                       _p(M, _D), _p(R, _D), _p(Q, _D))
     return M, R, Q
 
@@ -181,15 +186,18 @@ def groups(skey, tree: Octree, gs, delta=3, cmax=None):
     return gf[: ng + 1].copy()
 
 
-def lists(qs, gfirst, theta, tree: Octree):
-    """CSR interaction lists per group: (pc_off, pc_list, pp_off, pp_list)."""
+def lists(qs, gfirst, theta, tree: Octree, gsel=None):
+    """CSR interaction lists per group: (pc_off, pc_list, pp_off, pp_list).  gsel: walk only these
+    groups (CSR entry k = group gsel[k]); default all groups in order."""
     qs = np.ascontiguousarray(qs, dtype=np.uint32)
     gfirst = np.ascontiguousarray(gfirst, dtype=np.int64)
     n = qs.shape[1]
     ng = gfirst.shape[0] - 1
-    pc_off = np.zeros(ng + 1, np.int64); pp_off = np.zeros(ng + 1, np.int64)
-    args = (n, _p(qs, _U32), ng, _p(gfirst, _I64), float(theta), tree.nn, _p(tree.level, _I32),
-            _p(tree.corner, _U32), _p(tree.child, _I64), _p(tree.nchild, _I32))
+    gsel = None if gsel is None else np.ascontiguousarray(gsel, dtype=np.int64)
+    nsel = ng if gsel is None else gsel.shape[0]
+    pc_off = np.zeros(nsel + 1, np.int64); pp_off = np.zeros(nsel + 1, np.int64)
+    args = (n, _p(qs, _U32), ng, _p(gfirst, _I64), nsel, _p(gsel, _I64), float(theta), tree.nn,
+            _p(tree.level, _I32), _p(tree.corner, _U32), _p(tree.child, _I64), _p(tree.nchild, _I32))
     lib().orc_lists(*args, _p(pc_off, _I64), _p(pp_off, _I64), None, None)
     pc = np.zeros(max(1, pc_off[-1]), np.int64); pp = np.zeros(max(1, pp_off[-1]), np.int64)
     lib().orc_lists(*args, _p(pc_off, _I64), _p(pp_off, _I64), _p(pc, _I64), _p(pp, _I64))
@@ -208,6 +216,7 @@ class TreeResult:
     R: np.ndarray
     Q: np.ndarray
     gfirst: np.ndarray    # walk groups: first sorted index of each, then n
+    gsel: np.ndarray      # groups whose lists and forces were evaluated (None: all)
     pc_off: np.ndarray
     pc_list: np.ndarray
     pp_off: np.ndarray
@@ -217,26 +226,47 @@ class TreeResult:
 
 
 def tree_forces(x, m, *, G=1.0, eps=0.0, theta=0.7, lcap=16, gs=32, quad=True, delta=3, cmax=None,
-                want_forces=True):
-    """Whole canonical tree pipeline; returns every intermediate and a, phi."""
+                want_forces=True, groups_sel=None, timings=None):
+    """Whole canonical tree pipeline; returns every intermediate and a, phi.
+
+    groups_sel: walk groups (indices into the canonical groups) whose lists and forces are evaluated;
+    default all.  The box, keys, order, octree, moments and groups always cover every particle;
+    a and phi are zero outside the selected groups' particles.  timings: a dict that receives the
+    wall time of each stage."""
+    import time
+    T = timings if timings is not None else {}
+    t = time.perf_counter()
+
+    def lap(name):
+        nonlocal t
+        now = time.perf_counter()
+        T[name] = now - t
+        t = now
+
     x = _f64(x); m = _f64(m)
     n = m.shape[0]
-    lo, k = box(x)
-    q, key = keys(x, lo, k)
-    perm = sort(key)
-    tr = octree(key[perm], lcap)
-    M, R, Q = moments(tr, perm, x, m, lo, k)
+    lo, k = box(x); lap("box")
+    q, key = keys(x, lo, k); lap("keys")
+    perm = sort(key); lap("sort")
+    skey = key[perm]
+    tr = octree(skey, lcap); lap("octree")
+    M, R, Q = moments(tr, perm, x, m, lo, k); lap("moments")
+    gf = groups(skey, tr, gs, delta, cmax); lap("groups")
+    del skey
     qs = np.ascontiguousarray(q[:, perm])
-    gf = groups(key[perm], tr, gs, delta, cmax)
-    pc_off, pc, pp_off, pp = lists(qs, gf, theta, tr)
+    gsel = None if groups_sel is None else np.ascontiguousarray(groups_sel, dtype=np.int64)
+    pc_off, pc, pp_off, pp = lists(qs, gf, theta, tr, gsel); lap("lists")
+    del qs
     a = np.zeros((3, n)); phi = np.zeros(n)
     if want_forces:
-        lib().orc_tree_forces(n, _p(x, _D), _p(m, _D), _p(perm, _I64), gf.shape[0] - 1, _p(gf, _I64), tr.nn,
+        lib().orc_tree_forces(n, _p(x, _D), _p(m, _D), _p(perm, _I64), gf.shape[0] - 1, _p(gf, _I64),
+                              0 if gsel is None else gsel.shape[0], _p(gsel, _I64), tr.nn,
                               _p(M, _D), _p(R, _D), _p(Q, _D), _p(tr.first, _I64),
                               _p(tr.count, _I64), _p(pc_off, _I64), _p(pc, _I64),
                               _p(pp_off, _I64), _p(pp, _I64), float(G), float(eps),
                               1 if quad else 0, _p(a, _D), _p(phi, _D))
-    return TreeResult(lo, k, q, key, perm, tr, M, R, Q, gf, pc_off, pc, pp_off, pp, a, phi)
+    lap("forces")
+    return TreeResult(lo, k, q, key, perm, tr, M, R, Q, gf, gsel, pc_off, pc, pp_off, pp, a, phi)
 
 
 def tree_accel(x, m, **kw):
@@ -307,8 +337,8 @@ def tree_forces_frozen(r: TreeResult, x, m, *, G=1.0, eps=0.0, quad=True):
     M, R, Q = moments(r.tree, r.perm, x, m, r.lo, r.k)
     a = np.zeros((3, n)); phi = np.zeros(n)
     gf, tr = r.gfirst, r.tree
-    lib().orc_tree_forces(n, _p(x, _D), _p(m, _D), _p(r.perm, _I64), gf.shape[0] - 1, _p(gf, _I64), tr.nn,
-                          _p(M, _D), _p(R, _D), _p(Q, _D), _p(tr.first, _I64), _p(tr.count, _I64),
+    lib().orc_tree_forces(n, _p(x, _D), _p(m, _D), _p(r.perm, _I64), gf.shape[0] - 1, _p(gf, _I64), 0, None,
+                          tr.nn, _p(M, _D), _p(R, _D), _p(Q, _D), _p(tr.first, _I64), _p(tr.count, _I64),
                           _p(r.pc_off, _I64), _p(r.pc_list, _I64), _p(r.pp_off, _I64), _p(r.pp_list, _I64),
                           float(G), float(eps), 1 if quad else 0, _p(a, _D), _p(phi, _D))
     return a, phi

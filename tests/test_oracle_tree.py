@@ -308,7 +308,7 @@ def _single_cell_case(orc, D, quad, direction):
     pp_off = np.array([0, 1, 1], np.int64); pp = np.array([0], np.int64)
     a = np.zeros((3, n)); phi = np.zeros(n)
     P = orc._p
-    orc.lib().orc_tree_forces(n, P(x, orc._D), P(m, orc._D), P(perm, orc._I64), 2, P(gf, orc._I64), 2,
+    orc.lib().orc_tree_forces(n, P(x, orc._D), P(m, orc._D), P(perm, orc._I64), 2, P(gf, orc._I64), 0, None, 2,
                               P(M, orc._D), P(R, orc._D), P(Q, orc._D), P(first, orc._I64),
                               P(count, orc._I64), P(pc_off, orc._I64), P(pc, orc._I64),
                               P(pp_off, orc._I64), P(pp, orc._I64), 1.0, 0.0,
@@ -363,3 +363,32 @@ def test_plain_config_force_error(orc):
     e = np.linalg.norm(r.a - a, axis=0) / np.linalg.norm(a, axis=0)
     assert np.median(e) < 1e-3
     assert np.median(np.abs(r.phi - phi) / np.abs(phi)) < 1e-3
+
+
+def test_group_selection_equals_full_walk(orc):
+    """Lists and forces of a selection of walk groups (any order) are those of the
+    full walk for the same groups, bit for bit; other particles are untouched."""
+    x, _, m = inputs.galaxy(6000, 31)
+    x = x.numpy(); m = m.numpy()
+    kw = dict(eps=0.02, theta=0.7, lcap=16, gs=32, quad=True)
+    full = orc.tree_forces(x, m, **kw)
+    ng = len(full.gfirst) - 1
+    sel = np.random.default_rng(5).permutation(ng)[: ng // 5]
+    part = orc.tree_forces(x, m, groups_sel=sel, **kw)
+    np.testing.assert_array_equal(part.gfirst, full.gfirst)
+    touched = np.zeros(x.shape[1], bool)
+    for k, g in enumerate(sel):
+        np.testing.assert_array_equal(part.pc_list[part.pc_off[k]: part.pc_off[k + 1]],
+                                      full.pc_list[full.pc_off[g]: full.pc_off[g + 1]])
+        np.testing.assert_array_equal(part.pp_list[part.pp_off[k]: part.pp_off[k + 1]],
+                                      full.pp_list[full.pp_off[g]: full.pp_off[g + 1]])
+        touched[full.perm[full.gfirst[g]: full.gfirst[g + 1]]] = True
+    np.testing.assert_array_equal(part.a[:, touched], full.a[:, touched])
+    np.testing.assert_array_equal(part.phi[touched], full.phi[touched])
+    assert np.all(part.a[:, ~touched] == 0) and np.all(part.phi[~touched] == 0)
+
+
+def test_sort_matches_stable_library_sort(orc):
+    """(key, original index) order equals a stable library sort of the keys."""
+    key = np.random.default_rng(8).integers(0, 50, 20000).astype(np.uint64)
+    np.testing.assert_array_equal(orc.sort(key), np.argsort(key, kind="stable"))
