@@ -67,7 +67,8 @@ typedef enum {
     TREE_ERR_ARG = 1,       /* invalid argument: null pointer, size or parameter */
     TREE_ERR_CUDA = 2,      /* a CUDA runtime call failed */
     TREE_ERR_ALLOC = 3,     /* device memory allocation failed */
-    TREE_ERR_CAPACITY = 4,  /* n exceeds the workspace's n_max */
+    TREE_ERR_CAPACITY = 4,  /* a size exceeds a fixed capacity (the workspace's n_max; the
+                               no-allocation direct sum's target limit) */
     TREE_ERR_STATE = 5,     /* call order violated (e.g. tree_forces before tree_moments) */
     TREE_ERR_DEVICE = 6     /* tree_get_status: the device status word is non-zero */
 } tree_status_t;
@@ -77,7 +78,8 @@ typedef enum {
 #define TREE_DEV_STACK     0x02 /* a walk stack overflowed: forces are incomplete */
 #define TREE_DEV_NODES     0x04 /* node capacity reached: deep cells became large leaves
                                    (forces stay correct, the tree is not canonical) */
-#define TREE_DEV_TIMEOUT   0x08 /* a bounded device-side wait gave up: results invalid */
+#define TREE_DEV_TIMEOUT   0x08 /* a bounded device-side wait gave up: the results of that call are
+                                   invalid (the kernels after the wait returned without work) */
 #define TREE_DEV_LIST      0x10 /* interaction-list capacity exceeded */
 
 typedef enum { TREE_F32 = 0, TREE_F64 = 1 } tree_dtype_t;
@@ -135,7 +137,9 @@ typedef struct {
 #define TREE_PHASE_DIAG 8    /* diagnostics reductions */
 #define TREE_PHASE_DIRECT 9  /* direct summation */
 #define TREE_PHASE_ADJOINT 10 /* tree_forces_adjoint */
-#define TREE_NPHASES 11
+#define TREE_PHASE_H2D 11    /* leapfrog_step_host: copies of the state to the device */
+#define TREE_PHASE_D2H 12    /* leapfrog_step_host: copies back after the walk (x's copy overlaps the step) */
+#define TREE_NPHASES 13
 
 /* Fills *p with the defaults: G = 1, eps = 0.01, theta = 0.7, order = 2,
  * leaf_cap = 16, group_size = 32, stack_depth = 1024, precision = TREE_F32,
@@ -221,6 +225,16 @@ tree_status_t tree_forces_adjoint(TreeWorkspace *ws, const void *a_bar, const vo
 tree_status_t leapfrog_adjoint_step(TreeWorkspace *ws, void *x_bar, void *v_bar, void *a_bar, void *m_bar,
                                     const void *phi_bar, double tau, void *stream);
 
+/* Vector-Jacobian product of the potential energy W = 1/2 sum m_i phi_i
+ * (out[1] of tree_diagnostics; not part of the paper): given w_bar (device
+ * double[1], the cotangent of W), writes phi_bar[i] = w_bar m_i / 2 (the
+ * cotangent to pass on to tree_forces_adjoint or leapfrog_adjoint_step) and
+ * adds w_bar phi_i / 2 to m_bar[i] (the explicit mass dependence at fixed
+ * phi).  m, phi, phi_bar, m_bar: device [n] of the workspace precision;
+ * phi_bar or m_bar may be NULL. */
+tree_status_t tree_energy_vjp(TreeWorkspace *ws, const void *m, const void *phi, const double *w_bar, int64_t n,
+                              void *phi_bar, void *m_bar, void *stream);
+
 /* tree_build + tree_moments + tree_forces on (x, m, n). */
 tree_status_t tree_accel(TreeWorkspace *ws, const void *x, const void *m, int64_t n,
                          void *a, void *phi, void *stream);
@@ -232,6 +246,20 @@ tree_status_t tree_accel(TreeWorkspace *ws, const void *x, const void *m, int64_
  * kick with the force write-back. */
 tree_status_t leapfrog_step(TreeWorkspace *ws, void *x, void *v, const void *m, void *a,
                             void *phi, double tau, int64_t n, void *stream);
+
+/* leapfrog_step on a state held in HOST memory (for callers whose particles
+ * live on the host between steps): x, v, a [3][n], m [n] and phi [n] (or
+ * NULL) are host arrays of the workspace precision -- page-locked
+ * (cudaHostAlloc / cudaHostRegister) for the copies to be asynchronous.  The
+ * workspace keeps device copies (allocated on the first call: 44 B per
+ * particle of n_max in FP32, 88 in FP64).  The call copies x, v, m, a to the
+ * device, runs the step, and copies x, v, a and phi back; x is final after
+ * the drift, so its copy back runs on a second stream under the tree build
+ * and walk.  diag (host double[8], or NULL) receives tree_diagnostics of the
+ * new state.  Asynchronous on stream: the host arrays must not be used until
+ * the stream has run (the stream waits for every copy). */
+tree_status_t leapfrog_step_host(TreeWorkspace *ws, void *x, void *v, const void *m, void *a, void *phi,
+                                 double tau, int64_t n, double *diag, void *stream);
 
 /* FP64 reductions over the caller's arrays (precision of ws):
  * out[0] = E_kin = 1/2 sum m |v|^2, out[1] = W = 1/2 sum m phi,
@@ -263,23 +291,34 @@ tree_status_t leapfrog_graph_launch(TreeWorkspace *ws, void *stream);
  * offsets as in tree_set_segments) for every leaf_cap in {4, 8, 16},
  * group_size in {16, 32, 64} and stack_depth in {512, 1024}, the other
  * parameters taken from base, each leaf_cap in a temporary workspace of
- * n_max = n.  *best = the fastest candidate whose walks set no device status
- * bit.  table (host double[*ncand][4], may be NULL): rows (leaf_cap,
- * group_size, stack_depth, ms per evaluation; inf if rejected); *ncand in:
- * rows available, out: candidates tried.  Synchronises the device. */
+ * n_max = n.  Leaf capacity and group size change the cells that pass the
+ * opening criterion of Sec. 2, so they change the force error: every
+ * candidate's accelerations are compared with the FP64 direct sum of Eq. 1
+ * (each target against its own system) on a fixed sample of up to 512
+ * targets (16 systems x 32 for ensembles), and the median relative error
+ * |a - a_direct| / |a_direct| is taken.  *best = the fastest candidate whose
+ * walks set no device status bit and whose median error is <= max_err
+ * (max_err <= 0: no error bound).  table (host double[*ncand][5], may be
+ * NULL): rows (leaf_cap, group_size, stack_depth, ms per evaluation, median
+ * error), ms = inf for a rejected candidate, error = inf when its walk set a
+ * status bit; *ncand in: rows available, out: candidates tried.
+ * Synchronises the device.  Errors: TREE_ERR_DEVICE when no candidate
+ * qualifies. */
 tree_status_t tree_autotune(const TreeParams *base, int64_t nseg, const int64_t *offsets, const void *x,
-                            const void *m, int64_t n, int32_t reps, TreeParams *best, double *table,
-                            int32_t *ncand, void *stream);
+                            const void *m, int64_t n, int32_t reps, double max_err, TreeParams *best,
+                            double *table, int32_t *ncand, void *stream);
 
 /* Boxes of the last build, one per system: lo host double[nseg][3], k host
  * int32[nseg] (L = 2^k); either may be NULL.  Synchronises the device. */
 tree_status_t tree_export_boxes(TreeWorkspace *ws, double *lo, int32_t *k);
 
 /* Direct summation of Eq. 1 on the GPU, j != i, for nt targets (indices into
- * x, device int64[nt]) against all n sources.  dtype TREE_F32: FP32 pair terms,
- * compensated FP32 sums per source chunk, chunks combined in FP64;
- * TREE_F64: FP64 throughout.  a_out: device double [3][nt]; phi_out: device
- * double [nt] or NULL.  Uses and overwrites scratch in ws. */
+ * x, device int64[nt], each expected in [0, n)) against all n sources.
+ * dtype TREE_F32: FP32 pair terms, compensated FP32 sums per source chunk,
+ * chunks combined in FP64; TREE_F64: FP64 throughout.  a_out: device double
+ * [3][nt]; phi_out: device double [nt] or NULL.  A target index outside
+ * [0, n) reads nothing and gets NaN in its outputs.  Uses and overwrites
+ * scratch in ws. */
 tree_status_t tree_direct_forces(TreeWorkspace *ws, const void *x, const void *m, int64_t n,
                                  int32_t dtype, const int64_t *targets, int64_t nt,
                                  double *a_out, double *phi_out, void *stream);
@@ -302,8 +341,10 @@ tree_status_t tree_timing_read(TreeWorkspace *ws, double *ms, int64_t *calls, in
  * device memory: it needs no workspace and calls no allocator.  This entry
  * has no counterpart in the paper; it exists for applications whose own
  * memory pool owns the GPU, or code that may only touch buffers it is given.
- * x [3][n], m [n] of dtype; targets device int64[nt]; G, eps as in Eq. 1;
- * a_out device double [3][nt]; phi_out device double [nt] or NULL.
+ * x [3][n], m [n] of dtype; targets device int64[nt], each expected in
+ * [0, n) (an index outside gets NaN outputs and reads nothing); G, eps as
+ * for tree_direct_forces; a_out device double [3][nt]; phi_out device double
+ * [nt] or NULL.
  * Scratch is a fixed 4 MiB array inside the library, present on every GPU
  * that loads it until the process exits.  At most TREE_NOALLOC_MAX_TARGETS
  * targets per call (TREE_ERR_CAPACITY beyond); any n >= 1 sources.
@@ -316,6 +357,20 @@ tree_status_t tree_timing_read(TreeWorkspace *ws, double *ms, int64_t *calls, in
 tree_status_t tree_direct_forces_noalloc(const void *x, const void *m, int64_t n, int32_t dtype, double G,
                                          double eps, const int64_t *targets, int64_t nt, double *a_out,
                                          double *phi_out, void *stream);
+
+/* Bounded waits (not part of the paper).  Every device-side wait of the build
+ * (the decoupled look-backs of the sort passes, the octree levels and the
+ * walk-group scan) gives up after a limit of clock cycles: it then sets
+ * TREE_DEV_TIMEOUT, the rest of its own kernel writes only in bounds, and
+ * every later kernel of that build, force or gradient call returns without
+ * touching the tree -- the call's results are invalid, the context stays
+ * usable and the next build starts clean.  wait_cycles > 0 sets the limit
+ * (default 2e9 cycles, about 1 s); 0 keeps it.  withhold_pass and
+ * withhold_tile >= 0 make that tile of that sort pass (0..9) skip publishing
+ * its look-back words, so the tiles after it run into the limit: a test of
+ * the timeout path that needs no fault; -1 for both turns it off.
+ * Synchronises the device.  Errors: TREE_ERR_ARG. */
+tree_status_t tree_set_waits(TreeWorkspace *ws, int64_t wait_cycles, int32_t withhold_pass, int64_t withhold_tile);
 
 /* Synchronises the device, returns TREE_OK if the device status word is 0,
  * else TREE_ERR_DEVICE; *status (host) receives the word.  clear != 0 resets
@@ -346,6 +401,18 @@ tree_status_t tree_export_moments(TreeWorkspace *ws, double *M, double *R, doubl
 tree_status_t tree_export_lists(TreeWorkspace *ws, int64_t *pc_off, int32_t *pc_list,
                                 int64_t *pp_off, int32_t *pp_list, void *stream);
 
+/* Copies the lists of selected groups only (what tree_export_lists gives for
+ * those groups): gsel (host int64[nsel], each 0 <= gsel[k] < n_groups) names
+ * the groups; pc_off, pp_off (host int64[nsel+1]) receive CSR offsets in
+ * selection order; pc_list, pp_list (device int32, capacity pc_off[nsel],
+ * pp_off[nsel]) receive the far-cell and near-leaf entries of group gsel[k]
+ * at [off[k], off[k+1]), in walk order.  With pc_list = pp_list = NULL only
+ * the offsets are written (to size the buffers).  Synchronises the stream.
+ * Errors: TREE_ERR_STATE without stored lists, TREE_ERR_ARG for a group out
+ * of range. */
+tree_status_t tree_export_lists_groups(TreeWorkspace *ws, int64_t nsel, const int64_t *gsel, int64_t *pc_off,
+                                       int32_t *pc_list, int64_t *pp_off, int32_t *pp_list, void *stream);
+
 /* Copies the per-group records of the last walk into a caller device buffer
  * out (uint32 [4][n_groups]): row 0 far cells (PC list length), row 1 near
  * particles (PP sources, self included), row 2 deepest walk stack, row 3
@@ -361,6 +428,14 @@ tree_status_t tree_export_groups(TreeWorkspace *ws, uint32_t *gfirst, void *stre
  * "node of level l is far" <=> d2 >= D_l, where D_l = min{d : s_l^2 < fl(theta^2 d)}.
  * D (host int64[22]); theta = 0 gives INT64_MAX everywhere. */
 tree_status_t tree_mac_table(double theta, int64_t *D);
+
+/* Measured FP32 FMA throughput of the current GPU in TFLOP/s (2 flops per
+ * FMA), the roofline denominator of the FP32 walk (not part of the paper):
+ * register-only chains of fmaf (scalar) and of packed __ffma2_rn (packed) in
+ * four waves of resident blocks, best of three timed launches after one
+ * warm-up.  Either pointer (host) may be NULL.  Synchronous; takes well
+ * under a second. */
+tree_status_t tree_fp32_peak(double *tflops_scalar, double *tflops_packed);
 
 /* Static string for a status code. */
 const char *tree_status_string(tree_status_t s);

@@ -10,8 +10,9 @@ moments follow x and m).
 Memory: the forward pass keeps (x, v, a) every ``ckpt`` steps; the backward
 pass recomputes each segment from its checkpoint, then walks it in reverse,
 rebuilding the tree (with interaction lists) at every state and calling the
-library's reverse leapfrog step.  All arithmetic runs in libtreegb kernels;
-this module only orders the calls and handles the cotangents of W.
+library's reverse leapfrog step.  All arithmetic runs in libtreegb kernels
+(the cotangents of W included: tree_energy_vjp); this module only orders the
+calls.
 """
 from __future__ import annotations
 
@@ -49,9 +50,8 @@ class TreeLeapfrog(torch.autograd.Function):
         mb = torch.zeros_like(m)
         pb = None
         if gW is not None:
-            w = gW.detach().to(dt)
-            pb = (0.5 * w * m).contiguous()          # d(1/2 sum m phi)/d phi
-            mb += 0.5 * w * phiK                      # d(1/2 sum m phi)/d m at fixed phi
+            # phi_bar = gW m / 2 and m_bar += gW phi / 2, the VJP of W = 1/2 sum m phi
+            pb = ws.energy_vjp(m, phiK, gW.detach().to(torch.float64).reshape(1).contiguous(), m_bar=mb)
         starts = sorted(ckpts)
         for si in range(len(starts) - 1, -1, -1):
             s0 = starts[si]

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtreegb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "build.cu", "groups.cu", "moments.cu", "integrate.cu", "adjoint.cu", "walk_f32.cu",
-           "walk_f64.cu"]
+           "walk_f64.cu", "peak.cu"]
 
 
 def nvcc() -> str:

@@ -312,7 +312,9 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_force_vjp(const AdjArgs A) {
 template <typename Real>
 __global__ void __launch_bounds__(256) k_cot_gather(const Real *__restrict__ abar, const Real *__restrict__ phibar,
                                                     const uint32_t *__restrict__ perm, int64_t n,
-                                                    typename AdjVec<Real>::V4 *__restrict__ cot) {
+                                                    typename AdjVec<Real>::V4 *__restrict__ cot,
+                                                    const uint32_t *__restrict__ ctr) {
+    if (aborted(ctr, kStageAfter)) return;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t i = perm[s];
         typename AdjVec<Real>::V4 c;
@@ -330,6 +332,7 @@ __global__ void __launch_bounds__(256) k_cot_push(int L, const uint32_t *__restr
                                                   const typename AdjVec<Real>::V4 *__restrict__ spos,
                                                   double *__restrict__ ccot, double *__restrict__ xg,
                                                   double *__restrict__ mg, int64_t n) {
+    if (aborted(ctr, kStageAfter)) return;
     const uint32_t start = ctr[kCtrLevelStart + L], end = ctr[kCtrLevelStart + L + 1];
     for (uint32_t node = start + blockIdx.x * blockDim.x + threadIdx.x; node < end;
          node += gridDim.x * blockDim.x) {
@@ -390,7 +393,9 @@ __global__ void __launch_bounds__(256) k_cot_push(int L, const uint32_t *__restr
 template <typename Real>
 __global__ void __launch_bounds__(256) k_grad_scatter(const double *__restrict__ xt, const double *__restrict__ xg,
                                                       const double *__restrict__ mg, const uint32_t *__restrict__ perm,
-                                                      int64_t n, Real *__restrict__ xbar, Real *__restrict__ mbar) {
+                                                      int64_t n, Real *__restrict__ xbar, Real *__restrict__ mbar,
+                                                      const uint32_t *__restrict__ ctr) {
+    if (aborted(ctr, kStageAfter)) return;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t i = perm[s];
         if (xbar) {
@@ -412,7 +417,7 @@ static cudaError_t adjoint_impl(TreeWorkspace *ws, const void *abar, const void 
     if ((e = cudaMemsetAsync(ws->adj_ccot, 0, 10 * cap * sizeof(double), s)) != cudaSuccess) return e;
     const int nb = grid_for(n, 256, 152 * 8);
     k_cot_gather<Real><<<nb, 256, 0, s>>>((const Real *)abar, (const Real *)phibar, ws->idx, n,
-                                          (typename AdjVec<Real>::V4 *)ws->adj_cot);
+                                          (typename AdjVec<Real>::V4 *)ws->adj_cot, ws->ctr);
     AdjArgs A;
     A.n = n;
     A.ngroups = ws->list_groups;
@@ -438,7 +443,7 @@ static cudaError_t adjoint_impl(TreeWorkspace *ws, const void *abar, const void 
                                              (const typename AdjVec<Real>::V4 *)ws->spos, ws->adj_ccot, ws->adj_xg,
                                              ws->adj_mg, n);
     k_grad_scatter<Real><<<nb, 256, 0, s>>>(ws->adj_xt, ws->adj_xg, ws->adj_mg, ws->idx, n, (Real *)xbar,
-                                            (Real *)mbar);
+                                            (Real *)mbar, ws->ctr);
     ws->launches += 3 + kLevels;
     return cudaGetLastError();
 }
@@ -480,6 +485,32 @@ cudaError_t launch_adjoint_step(TreeWorkspace *ws, void *xbar, void *vbar, void 
                                          (const double *)phibar, tau, s);
     return adjoint_step_impl<float>(ws, (float *)xbar, (float *)vbar, (float *)abar, (float *)mbar,
                                     (const float *)phibar, tau, s);
+}
+
+// Cotangents of W = 1/2 sum m phi (tree_energy_vjp): phi_bar = w_bar m / 2,
+// m_bar += w_bar phi / 2.
+template <typename Real>
+__global__ void __launch_bounds__(256) k_energy_vjp(const Real *__restrict__ m, const Real *__restrict__ phi,
+                                                    const double *__restrict__ wbar, int64_t n,
+                                                    Real *__restrict__ phibar, Real *__restrict__ mbar) {
+    const Real h = (Real)(0.5 * wbar[0]);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (phibar) phibar[i] = h * m[i];
+        if (mbar) mbar[i] += h * phi[i];
+    }
+}
+
+cudaError_t launch_energy_vjp(TreeWorkspace *ws, const void *m, const void *phi, const double *wbar, int64_t n,
+                              void *phibar, void *mbar, cudaStream_t s) {
+    const int nb = grid_for(n, 256, 152 * 8);
+    if (ws->p.precision == TREE_F64)
+        k_energy_vjp<double><<<nb, 256, 0, s>>>((const double *)m, (const double *)phi, wbar, n, (double *)phibar,
+                                                (double *)mbar);
+    else
+        k_energy_vjp<float><<<nb, 256, 0, s>>>((const float *)m, (const float *)phi, wbar, n, (float *)phibar,
+                                               (float *)mbar);
+    ws->launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint(TreeWorkspace *ws, const void *abar, const void *phibar, void *xbar, void *mbar,

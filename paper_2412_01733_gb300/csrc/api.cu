@@ -4,7 +4,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -74,12 +76,18 @@ void free_all(TreeWorkspace *ws) {
                     ws->gkey, ws->gbucket, ws->gfirst, ws->plev, ws->ccount, ws->coff, ws->gscan_status,
                     ws->adj_cot, ws->adj_xt, ws->adj_xg, ws->adj_mg, ws->adj_ccot, ws->pleaf, ws->nparent,
                     ws->seg_off, ws->seg_cstart, ws->seg_bchunk, ws->seg_bfirst, ws->seg_part,
-                    ws->seg_digit_off, ws->cmask, ws->morder, ws->mbucket, ws->xm};
+                    ws->seg_digit_off, ws->cmask, ws->morder, ws->mbucket, ws->xm, ws->hs_x, ws->hs_v,
+                    ws->hs_m, ws->hs_a, ws->hs_phi, ws->hs_diag, ws->dctl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ws->graph_exec) cudaGraphExecDestroy(ws->graph_exec);
     if (ws->graph) cudaGraphDestroy(ws->graph);
     if (ws->cap_stream) cudaStreamDestroy(ws->cap_stream);
+    if (ws->copy_stream) cudaStreamDestroy(ws->copy_stream);
+    if (ws->ev_drift) cudaEventDestroy(ws->ev_drift);
+    if (ws->ev_xback) cudaEventDestroy(ws->ev_xback);
+    ws->copy_stream = nullptr;
+    ws->ev_drift = ws->ev_xback = nullptr;
     ws->graph_exec = nullptr;
     ws->graph = nullptr;
     ws->cap_stream = nullptr;
@@ -199,7 +207,7 @@ const char *tree_status_string(tree_status_t s) {
         case TREE_ERR_ARG: return "invalid argument";
         case TREE_ERR_CUDA: return "CUDA runtime error";
         case TREE_ERR_ALLOC: return "device allocation failed";
-        case TREE_ERR_CAPACITY: return "n exceeds the workspace capacity";
+        case TREE_ERR_CAPACITY: return "size exceeds a fixed capacity (workspace n_max, or the no-allocation target limit)";
         case TREE_ERR_STATE: return "call order violated";
         case TREE_ERR_DEVICE: return "device status word is set";
     }
@@ -267,7 +275,7 @@ tree_status_t tree_workspace_create(int64_t n_max, const TreeParams *p, TreeWork
               dalloc(&ws->ccount, (size_t)chunks_max) && dalloc(&ws->coff, (size_t)chunks_max) &&
               dalloc(&ws->cmask, 2 * (size_t)chunks_max) &&
               dalloc(&ws->gscan_status, (size_t)(chunks_max / 2048 + 2)) &&
-              dalloc(&ws->dmac, kLevels);
+              dalloc(&ws->dmac, kLevels) && dalloc(&ws->dctl, 1);
     ws->chunks_cap = chunks_max;
     ws->box_cap = 1;
     if (!ok) {
@@ -276,8 +284,10 @@ tree_status_t tree_workspace_create(int64_t n_max, const TreeParams *p, TreeWork
         cudaGetLastError();
         return TREE_ERR_ALLOC;
     }
+    const DevCtl ctl{kWaitCycles, -1};
     if (cudaMemset(ws->dstatus, 0, sizeof(int32_t)) != cudaSuccess ||
-        cudaMemset(ws->stats, 0, kStatCount * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMemset(ws->stats, 0, kStatCount * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemcpy(ws->dctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice) != cudaSuccess) {
         free_all(ws);
         delete ws;
         return TREE_ERR_CUDA;
@@ -576,6 +586,15 @@ tree_status_t leapfrog_adjoint_step(TreeWorkspace *ws, void *x_bar, void *v_bar,
     return TREE_OK;
 }
 
+tree_status_t tree_energy_vjp(TreeWorkspace *ws, const void *m, const void *phi, const double *w_bar, int64_t n,
+                              void *phi_bar, void *m_bar, void *stream) {
+    if (!ws || n < 0) return TREE_ERR_ARG;
+    if (n == 0) return TREE_OK;
+    if (!m || !phi || !w_bar || (!phi_bar && !m_bar)) return TREE_ERR_ARG;
+    TRY_CUDA(launch_energy_vjp(ws, m, phi, w_bar, n, phi_bar, m_bar, as_stream(stream)));
+    return TREE_OK;
+}
+
 tree_status_t tree_accel(TreeWorkspace *ws, const void *x, const void *m, int64_t n, void *a, void *phi,
                          void *stream) {
     if (!ws) return TREE_ERR_ARG;
@@ -587,15 +606,10 @@ tree_status_t tree_accel(TreeWorkspace *ws, const void *x, const void *m, int64_
     return tree_forces(ws, a, phi, 0, stream);
 }
 
-tree_status_t leapfrog_step(TreeWorkspace *ws, void *x, void *v, const void *m, void *a, void *phi, double tau,
-                            int64_t n, void *stream) {
-    if (!ws) return TREE_ERR_ARG;
-    if (!isfinite(tau)) return TREE_ERR_ARG;
-    tree_status_t stn = check_n(ws, n);
-    if (stn != TREE_OK) return stn;
-    if (n == 0) return TREE_OK;
-    if (!x || !v || !m || !a) return TREE_ERR_ARG;
-    cudaStream_t s = as_stream(stream);
+// First part of a step: the first kick and the drift (Eqs. 2-3), fused with
+// the box of the new positions.  After it, x holds r^{n+1} and is only read.
+static tree_status_t leapfrog_begin(TreeWorkspace *ws, void *x, void *v, const void *m, void *a, double tau,
+                                    int64_t n, cudaStream_t s) {
     ws->n = n;
     ws->built = false;
     ws->has_moments = false;
@@ -608,11 +622,15 @@ tree_status_t leapfrog_step(TreeWorkspace *ws, void *x, void *v, const void *m, 
                                  (size_t)tiles * kRadix * sizeof(uint32_t), s));
     TRY_CUDA(cudaMemsetAsync(ws->level_status, 0, (size_t)kLevels * ws->level_tiles_max * sizeof(uint32_t), s));
     // Eqs. 2-3 fused with the box of the new positions
-    {
-        PhaseScope ph(ws, TREE_PHASE_BOX, s);
-        TRY_CUDA(launch_kick_drift_box(ws, x, v, a, m, tau, n, s));
-    }
-    // Eq. 4: tree at r^{n+1}
+    PhaseScope ph(ws, TREE_PHASE_BOX, s);
+    TRY_CUDA(launch_kick_drift_box(ws, x, v, a, m, tau, n, s));
+    return TREE_OK;
+}
+
+// Rest of a step: the tree at r^{n+1} (Eq. 4) and the forces, written back
+// with the second kick (Eq. 5) fused in.
+static tree_status_t leapfrog_finish(TreeWorkspace *ws, const void *x, void *v, void *a, void *phi, double tau,
+                                     int64_t n, cudaStream_t s) {
     {
         PhaseScope ph(ws, TREE_PHASE_KEYS, s);
         TRY_CUDA(launch_keys(ws, x, n, s));
@@ -636,9 +654,77 @@ tree_status_t leapfrog_step(TreeWorkspace *ws, void *x, void *v, const void *m, 
         TRY_CUDA(launch_moments(ws, s));
     }
     ws->has_moments = true;
-    // forces written back with the Eq. 5 kick fused in
     WalkOut out{a, phi, v, 0.5 * tau};
     return walk(ws, kWalkForce, out, s);
+}
+
+tree_status_t leapfrog_step(TreeWorkspace *ws, void *x, void *v, const void *m, void *a, void *phi, double tau,
+                            int64_t n, void *stream) {
+    if (!ws) return TREE_ERR_ARG;
+    if (!isfinite(tau)) return TREE_ERR_ARG;
+    tree_status_t stn = check_n(ws, n);
+    if (stn != TREE_OK) return stn;
+    if (n == 0) return TREE_OK;
+    if (!x || !v || !m || !a) return TREE_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    tree_status_t st = leapfrog_begin(ws, x, v, m, a, tau, n, s);
+    if (st != TREE_OK) return st;
+    return leapfrog_finish(ws, x, v, a, phi, tau, n, s);
+}
+
+tree_status_t leapfrog_step_host(TreeWorkspace *ws, void *x, void *v, const void *m, void *a, void *phi, double tau,
+                                 int64_t n, double *diag, void *stream) {
+    if (!ws) return TREE_ERR_ARG;
+    if (!isfinite(tau)) return TREE_ERR_ARG;
+    tree_status_t st = check_n(ws, n);
+    if (st != TREE_OK) return st;
+    if (n == 0) return TREE_OK;
+    if (!x || !v || !m || !a) return TREE_ERR_ARG;
+    const size_t rs = ws->real_size, N = (size_t)ws->n_max;
+    if (!ws->hs_x) {
+        if (!(dalloc((unsigned char **)&ws->hs_x, 3 * N * rs) && dalloc((unsigned char **)&ws->hs_v, 3 * N * rs) &&
+              dalloc((unsigned char **)&ws->hs_m, N * rs) && dalloc((unsigned char **)&ws->hs_a, 3 * N * rs) &&
+              dalloc((unsigned char **)&ws->hs_phi, N * rs) && dalloc(&ws->hs_diag, 8))) {
+            cudaGetLastError();
+            return TREE_ERR_ALLOC;
+        }
+    }
+    if (!ws->copy_stream) TRY_CUDA(cudaStreamCreateWithFlags(&ws->copy_stream, cudaStreamNonBlocking));
+    if (!ws->ev_drift) TRY_CUDA(cudaEventCreateWithFlags(&ws->ev_drift, cudaEventDisableTiming));
+    if (!ws->ev_xback) TRY_CUDA(cudaEventCreateWithFlags(&ws->ev_xback, cudaEventDisableTiming));
+    cudaStream_t s = as_stream(stream);
+    const size_t b3 = 3 * (size_t)n * rs, b1 = (size_t)n * rs;
+    {
+        PhaseScope ph(ws, TREE_PHASE_H2D, s);
+        TRY_CUDA(cudaMemcpyAsync(ws->hs_x, x, b3, cudaMemcpyHostToDevice, s));
+        TRY_CUDA(cudaMemcpyAsync(ws->hs_v, v, b3, cudaMemcpyHostToDevice, s));
+        TRY_CUDA(cudaMemcpyAsync(ws->hs_m, m, b1, cudaMemcpyHostToDevice, s));
+        TRY_CUDA(cudaMemcpyAsync(ws->hs_a, a, b3, cudaMemcpyHostToDevice, s));
+    }
+    st = leapfrog_begin(ws, ws->hs_x, ws->hs_v, ws->hs_m, ws->hs_a, tau, n, s);
+    if (st != TREE_OK) return st;
+    // r^{n+1} is final once the drift has run: copy it back on a second
+    // stream while the tree is built and walked
+    TRY_CUDA(cudaEventRecord(ws->ev_drift, s));
+    TRY_CUDA(cudaStreamWaitEvent(ws->copy_stream, ws->ev_drift, 0));
+    TRY_CUDA(cudaMemcpyAsync(x, ws->hs_x, b3, cudaMemcpyDeviceToHost, ws->copy_stream));
+    TRY_CUDA(cudaEventRecord(ws->ev_xback, ws->copy_stream));
+    st = leapfrog_finish(ws, ws->hs_x, ws->hs_v, ws->hs_a, ws->hs_phi, tau, n, s);
+    if (st != TREE_OK) return st;
+    if (diag) {
+        PhaseScope ph(ws, TREE_PHASE_DIAG, s);
+        TRY_CUDA(launch_diagnostics(ws, ws->hs_x, ws->hs_v, ws->hs_m, ws->hs_phi, n, ws->hs_diag, s));
+    }
+    {
+        PhaseScope ph(ws, TREE_PHASE_D2H, s);
+        TRY_CUDA(cudaMemcpyAsync(v, ws->hs_v, b3, cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(cudaMemcpyAsync(a, ws->hs_a, b3, cudaMemcpyDeviceToHost, s));
+        if (phi) TRY_CUDA(cudaMemcpyAsync(phi, ws->hs_phi, b1, cudaMemcpyDeviceToHost, s));
+        if (diag) TRY_CUDA(cudaMemcpyAsync(diag, ws->hs_diag, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    // the caller's stream completes only after x's copy has landed too
+    TRY_CUDA(cudaStreamWaitEvent(s, ws->ev_xback, 0));
+    return TREE_OK;
 }
 
 tree_status_t tree_diagnostics(TreeWorkspace *ws, const void *x, const void *v, const void *m, const void *phi,
@@ -724,11 +810,94 @@ tree_status_t leapfrog_graph_launch(TreeWorkspace *ws, void *stream) {
     return TREE_OK;
 }
 
+namespace {
+// Force-error reference of the autotuner: the FP64 direct sum of Eq. 1 for a
+// fixed sample of targets, each against the sources of its own system.
+struct TuneRef {
+    int64_t nt = 0;
+    std::vector<int64_t> blk_first, blk_count, blk_src0, blk_src1;  // per system block
+    int64_t *tgt = nullptr;      // device [nt]
+    double *ref = nullptr;       // device, block b at 3 * blk_first[b]: [3][blk_count[b]]
+    double *err = nullptr;       // device [nt]
+    double *x64 = nullptr, *m64 = nullptr;  // FP64 copies of FP32 inputs
+    TreeWorkspace *ws = nullptr;  // scratch of the direct sums
+    ~TuneRef() {
+        if (tgt) cudaFree(tgt);
+        if (ref) cudaFree(ref);
+        if (err) cudaFree(err);
+        if (x64) cudaFree(x64);
+        if (m64) cudaFree(m64);
+        if (ws) tree_workspace_destroy(ws);
+    }
+};
+
+tree_status_t tune_reference(TuneRef &R, const TreeParams *base, int64_t nseg, const int64_t *offsets, const void *x,
+                             const void *m, int64_t n, cudaStream_t s) {
+    // up to 16 systems, evenly spaced, up to 512 targets in all, evenly spaced inside each system
+    const int64_t ns = nseg > 1 ? nseg : 1;
+    const int64_t nsys = ns < 16 ? ns : 16;
+    const int64_t per = nseg > 1 ? 32 : 512;
+    std::vector<int64_t> h;
+    for (int64_t j = 0; j < nsys; ++j) {
+        const int64_t b = j * ns / nsys;
+        const int64_t a0 = nseg > 1 ? offsets[b] : 0, a1 = nseg > 1 ? offsets[b + 1] : n;
+        const int64_t cnt = a1 - a0 < per ? a1 - a0 : per;
+        R.blk_first.push_back((int64_t)h.size());
+        R.blk_count.push_back(cnt);
+        R.blk_src0.push_back(a0);
+        R.blk_src1.push_back(a1);
+        for (int64_t k = 0; k < cnt; ++k) h.push_back(a0 + k * (a1 - a0) / cnt);
+    }
+    R.nt = (int64_t)h.size();
+    TreeParams p = *base;
+    p.node_cap = 0;
+    tree_status_t st = tree_workspace_create(1, &p, &R.ws);
+    if (st != TREE_OK) return st;
+    if (!dalloc(&R.tgt, (size_t)R.nt) || !dalloc(&R.ref, 3 * (size_t)R.nt) || !dalloc(&R.err, (size_t)R.nt))
+        return TREE_ERR_ALLOC;
+    TRY_CUDA(cudaMemcpyAsync(R.tgt, h.data(), h.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    const void *xr = x, *mr = m;
+    if (base->precision == TREE_F32) {
+        if (!dalloc(&R.x64, 3 * (size_t)n) || !dalloc(&R.m64, (size_t)n)) return TREE_ERR_ALLOC;
+        TRY_CUDA(launch_widen(R.ws, (const float *)x, 3 * n, R.x64, s));
+        TRY_CUDA(launch_widen(R.ws, (const float *)m, n, R.m64, s));
+        xr = R.x64;
+        mr = R.m64;
+    }
+    for (size_t b = 0; b < R.blk_first.size(); ++b)
+        TRY_CUDA(launch_direct_range(R.ws, xr, mr, n, R.blk_src0[b], R.blk_src1[b], TREE_F64, base->G, base->eps,
+                                     R.tgt + R.blk_first[b], R.blk_count[b], R.ref + 3 * R.blk_first[b], nullptr, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    return TREE_OK;
+}
+
+// Median relative error of the accelerations a ([3][n], base precision) over the sample.
+tree_status_t tune_error(TuneRef &R, const void *a, int64_t n, int dtype, cudaStream_t s, double *med) {
+    for (size_t b = 0; b < R.blk_first.size(); ++b)
+        TRY_CUDA(launch_rel_err(R.ws, a, n, dtype, R.tgt + R.blk_first[b], R.ref + 3 * R.blk_first[b],
+                                R.blk_count[b], R.err + R.blk_first[b], s));
+    std::vector<double> e((size_t)R.nt);
+    TRY_CUDA(cudaMemcpyAsync(e.data(), R.err, e.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    if (e.empty()) { *med = 0.0; return TREE_OK; }
+    // lower median: deterministic and a member of the sample
+    const size_t k = (e.size() - 1) / 2;
+    std::nth_element(e.begin(), e.begin() + k, e.end());
+    *med = e[k];
+    return TREE_OK;
+}
+}  // namespace
+
 tree_status_t tree_autotune(const TreeParams *base, int64_t nseg, const int64_t *offsets, const void *x,
-                            const void *m, int64_t n, int32_t reps, TreeParams *best, double *table,
+                            const void *m, int64_t n, int32_t reps, double max_err, TreeParams *best, double *table,
                             int32_t *ncand, void *stream) {
-    if (!base || !best || !x || !m || n <= 0 || reps < 1) return TREE_ERR_ARG;
+    if (!base || !best || !x || !m || n <= 0 || reps < 1 || isnan(max_err)) return TREE_ERR_ARG;
     if (table && !ncand) return TREE_ERR_ARG;
+    if (nseg > 1) {
+        if (!offsets || offsets[0] != 0 || offsets[nseg] != n) return TREE_ERR_ARG;
+        for (int64_t b = 0; b < nseg; ++b)
+            if (offsets[b + 1] <= offsets[b]) return TREE_ERR_ARG;
+    }
     tree_status_t st = check_params(base);
     if (st != TREE_OK) return st;
     cudaStream_t s = as_stream(stream);
@@ -736,6 +905,9 @@ tree_status_t tree_autotune(const TreeParams *base, int64_t nseg, const int64_t 
     const int32_t rows = table ? *ncand : 0;
     int32_t used = 0;
     double best_ms = INFINITY;
+    TuneRef R;
+    st = tune_reference(R, base, nseg, offsets, x, m, n, s);
+    if (st != TREE_OK) return st;
     void *a = nullptr;
     const size_t rs = base->precision == TREE_F64 ? 8 : 4;
     TRY_CUDA(cudaMalloc(&a, 3 * (size_t)n * rs));
@@ -759,7 +931,7 @@ tree_status_t tree_autotune(const TreeParams *base, int64_t nseg, const int64_t 
                 p.stack_depth = stacks[si];
                 st = tree_set_params(ws, &p);
                 if (st != TREE_OK) break;
-                double ms = INFINITY;
+                double ms = INFINITY, err = INFINITY;
                 int32_t dev = 0;
                 // one untimed evaluation, then reps timed ones
                 for (int r = 0; r <= reps && st == TREE_OK; ++r) {
@@ -776,12 +948,17 @@ tree_status_t tree_autotune(const TreeParams *base, int64_t nseg, const int64_t 
                 st = tree_get_status(ws, &dev, 1);
                 if (st == TREE_ERR_DEVICE) st = TREE_OK;  // the status bits decide below
                 if (st != TREE_OK) break;
-                if (dev == 0) ms = (double)t / reps;  // a candidate that overflowed its stack does not count
+                st = tune_error(R, a, n, p.precision, s, &err);
+                if (st != TREE_OK) break;
+                // a candidate that overflowed its stack, or whose forces miss the error bound, does not count
+                const bool ok = dev == 0 && (!(max_err > 0.0) || err <= max_err);
+                if (ok) ms = (double)t / reps;
                 if (table && used < rows) {
-                    table[4 * used + 0] = p.leaf_cap;
-                    table[4 * used + 1] = p.group_size;
-                    table[4 * used + 2] = p.stack_depth;
-                    table[4 * used + 3] = ms;
+                    table[5 * used + 0] = p.leaf_cap;
+                    table[5 * used + 1] = p.group_size;
+                    table[5 * used + 2] = p.stack_depth;
+                    table[5 * used + 3] = ok ? ms : INFINITY;
+                    table[5 * used + 4] = dev == 0 ? err : INFINITY;
                 }
                 ++used;
                 if (ms < best_ms) {
@@ -850,6 +1027,19 @@ tree_status_t tree_timing_read(TreeWorkspace *ws, double *ms, int64_t *calls, in
         if (calls) calls[ph] += 1;
     }
     if (launches) *launches = ws->timed_launches;
+    return TREE_OK;
+}
+
+tree_status_t tree_set_waits(TreeWorkspace *ws, int64_t wait_cycles, int32_t withhold_pass, int64_t withhold_tile) {
+    if (!ws || wait_cycles < 0) return TREE_ERR_ARG;
+    if ((withhold_pass < 0) != (withhold_tile < 0)) return TREE_ERR_ARG;
+    if (withhold_pass >= kSortPasses + kSegPassesMax || withhold_tile > 0xffffffffLL) return TREE_ERR_ARG;
+    TRY_CUDA(cudaDeviceSynchronize());
+    DevCtl ctl;
+    TRY_CUDA(cudaMemcpy(&ctl, ws->dctl, sizeof(ctl), cudaMemcpyDeviceToHost));
+    if (wait_cycles > 0) ctl.wait_cycles = wait_cycles;
+    ctl.withhold = withhold_pass < 0 ? -1 : (((long long)withhold_pass << 32) | (long long)withhold_tile);
+    TRY_CUDA(cudaMemcpy(ws->dctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice));
     return TREE_OK;
 }
 
@@ -947,6 +1137,40 @@ tree_status_t tree_export_groups(TreeWorkspace *ws, uint32_t *gfirst, void *stre
     TRY_CUDA(cudaMemcpy(&ng, ws->ctr + kCtrGroups, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     TRY_CUDA(cudaMemcpyAsync(gfirst, ws->gfirst, ((size_t)ng + 1) * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
                              as_stream(stream)));
+    return TREE_OK;
+}
+
+tree_status_t tree_export_lists_groups(TreeWorkspace *ws, int64_t nsel, const int64_t *gsel, int64_t *pc_off,
+                                       int32_t *pc_list, int64_t *pp_off, int32_t *pp_list, void *stream) {
+    if (!ws || nsel < 0 || (nsel > 0 && !gsel) || !pc_off || !pp_off) return TREE_ERR_ARG;
+    if (ws->list_groups < 0) return TREE_ERR_STATE;
+    const int64_t ng = ws->list_groups;
+    for (int64_t k = 0; k < nsel; ++k)
+        if (gsel[k] < 0 || gsel[k] >= ng) return TREE_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    // both offset tables, [2][ng + 1]
+    std::vector<int64_t> off((size_t)(2 * (ng + 1)));
+    TRY_CUDA(cudaMemcpyAsync(off.data(), ws->list_cnt, off.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    const int64_t *pco = off.data(), *ppo = off.data() + ng + 1;
+    pc_off[0] = 0;
+    pp_off[0] = 0;
+    for (int64_t k = 0; k < nsel; ++k) {
+        const int64_t g = gsel[k];
+        pc_off[k + 1] = pc_off[k] + (pco[g + 1] - pco[g]);
+        pp_off[k + 1] = pp_off[k] + (ppo[g + 1] - ppo[g]);
+    }
+    for (int64_t k = 0; k < nsel; ++k) {
+        const int64_t g = gsel[k];
+        const int64_t npc = pco[g + 1] - pco[g], npp = ppo[g + 1] - ppo[g];
+        if (pc_list && npc > 0)
+            TRY_CUDA(cudaMemcpyAsync(pc_list + pc_off[k], ws->pc_list + pco[g], (size_t)npc * sizeof(int32_t),
+                                     cudaMemcpyDeviceToDevice, s));
+        if (pp_list && npp > 0)
+            TRY_CUDA(cudaMemcpyAsync(pp_list + pp_off[k], ws->pp_list + ppo[g], (size_t)npp * sizeof(int32_t),
+                                     cudaMemcpyDeviceToDevice, s));
+    }
+    TRY_CUDA(cudaStreamSynchronize(s));
     return TREE_OK;
 }
 

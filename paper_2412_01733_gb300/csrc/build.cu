@@ -347,10 +347,13 @@ template <int MODE>
 __global__ void __launch_bounds__(kSortThreads, MODE == kPassSeg ? 2 : 3) k_onesweep(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t n, int shift, const uint32_t *__restrict__ digit_off,
-    uint32_t *status, uint32_t *ticket, int32_t *dstatus, const int64_t *__restrict__ seg_off, int64_t nseg) {
+    uint32_t *status, uint32_t *ticket, int32_t *dstatus, const int64_t *__restrict__ seg_off, int64_t nseg,
+    uint32_t *ctr, uint32_t pass, const DevCtl *__restrict__ ctl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem &S = *reinterpret_cast<SortSmem *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t stage = kStageSort0 + pass;
+    if (aborted(ctr, stage)) return;  // an earlier pass gave up a wait: its output is not a permutation
     for (int i = tid; i < (kSortThreads / 32) * kRadix; i += kSortThreads) (&S.whist[0][0])[i] = 0;
     if (tid == 0) S.tile = atomicAdd(ticket, 1u);
     __syncthreads();
@@ -411,12 +414,16 @@ __global__ void __launch_bounds__(kSortThreads, MODE == kPassSeg ? 2 : 3) k_ones
         const int d = tid;
         uint32_t *st = status + d;  // word of digit d in tile t is st[t * 256]
         uint32_t excl = 0;
+        const WaitCtx wc{dstatus, ctr, stage, ctl->wait_cycles};
+        // test injection: this tile keeps its words unpublished, so the tiles
+        // after it run into their wait limit
+        const bool publish = ctl->withhold != (((long long)pass << 32) | (long long)tile);
         if (tile == 0) {
-            st_release(st, kFlagInc | tcount);
+            if (publish) st_release(st, kFlagInc | tcount);
         } else {
-            st_release(st + (size_t)tile * kRadix, kFlagAgg | tcount);
-            excl = lookback_walk(st, kRadix, (int64_t)tile - 1, dstatus);
-            st_release(st + (size_t)tile * kRadix, kFlagInc | ((excl + tcount) & kValMask));
+            if (publish) st_release(st + (size_t)tile * kRadix, kFlagAgg | tcount);
+            excl = lookback_walk(st, kRadix, (int64_t)tile - 1, wc);
+            if (publish) st_release(st + (size_t)tile * kRadix, kFlagInc | ((excl + tcount) & kValMask));
         }
         S.gbase[d] = digit_off[d] + excl;
     }
@@ -495,19 +502,20 @@ cudaError_t launch_sort(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
         uint32_t *st = ws->sort_status + (size_t)p * ws->sort_tiles_max * kRadix;
         uint32_t *tk = ws->ctr + kCtrSortTicket + p;
         const unsigned g = (unsigned)tiles;
+        const uint32_t pu = (uint32_t)p;
         if (p == 0) {
             k_onesweep<kPassFirst><<<g, kSortThreads, smem, s>>>(kin, vin, kout, vout, n, 0,
                                                                  ws->hist + kSortPasses * kRadix, st, tk,
-                                                                 ws->dstatus, nullptr, 1);
+                                                                 ws->dstatus, nullptr, 1, ws->ctr, pu, ws->dctl);
         } else if (p < kSortPasses) {
             k_onesweep<kPassKey><<<g, kSortThreads, smem, s>>>(kin, vin, kout, vout, n, 8 * p,
                                                                ws->hist + kSortPasses * kRadix + p * kRadix, st, tk,
-                                                               ws->dstatus, nullptr, 1);
+                                                               ws->dstatus, nullptr, 1, ws->ctr, pu, ws->dctl);
         } else {
             const int q = p - kSortPasses;
             k_onesweep<kPassSeg><<<g, kSortThreads, smem, s>>>(kin, vin, kout, vout, n, 8 * q,
                                                                ws->seg_digit_off + q * kRadix, st, tk, ws->dstatus,
-                                                               ws->seg_off, ws->nseg);
+                                                               ws->seg_off, ws->nseg, ws->ctr, pu, ws->dctl);
         }
         uint64_t *tk_ = kin; kin = kout; kout = tk_;
         uint32_t *tv_ = vin; vin = vout; vout = tv_;
@@ -522,6 +530,7 @@ cudaError_t launch_sort(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
 // [off[b], off[b+1])), or the single root of all n particles.
 __global__ void k_tree_init(uint32_t *ctr, uint32_t *nfirst, uint32_t *ncount, uint32_t *nparent, int64_t n,
                             const int64_t *__restrict__ seg_off, int64_t nseg) {
+    if (aborted(ctr, kStageAfter)) return;
     const int t = threadIdx.x;
     if (blockIdx.x == 0) {
         if (t < kLevels + 1) {
@@ -572,9 +581,11 @@ __device__ __forceinline__ void octant_bounds(const uint64_t *__restrict__ skey,
 __global__ void __launch_bounds__(kLevelThreads) k_level(
     int L, const uint64_t *__restrict__ skey, uint32_t *__restrict__ nfirst, uint32_t *__restrict__ ncount,
     uint4 *__restrict__ ngeo, uint2 *__restrict__ nlink, uint32_t *__restrict__ nparent, uint32_t *ctr,
-    uint32_t *lstatus, uint32_t lcap, uint32_t node_cap, int32_t *dstatus) {
+    uint32_t *lstatus, uint32_t lcap, uint32_t node_cap, int32_t *dstatus, const DevCtl *__restrict__ ctl) {
     __shared__ uint32_t s_tile, s_excl, s_total;
     __shared__ uint32_t wt[32];
+    const uint32_t stage = kStageLevel0 + (uint32_t)L;
+    if (aborted(ctr, stage)) return;
     const uint32_t start = ctr[kCtrLevelStart + L];
     const uint32_t raw = ctr[kCtrLevelRawEnd + L], tr = ctr[kCtrLevelTrunc + L];
     const uint32_t end = raw < tr ? raw : tr;
@@ -613,7 +624,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(
         uint32_t tot;
         const uint32_t loc = block_exclusive_scan(nch, wt, &tot);
         if (tid == 0) {
-            s_excl = lookback_single(lstatus, tile, tot, dstatus);
+            s_excl = lookback_single(lstatus, tile, tot, WaitCtx{dstatus, ctr, stage, ctl->wait_cycles});
             s_total = tot;
         }
         __syncthreads();
@@ -656,7 +667,7 @@ cudaError_t launch_octree(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
         uint32_t *lst = ws->level_status + (size_t)L * ws->level_tiles_max;
         k_level<<<nb, kLevelThreads, 0, s>>>(L, ws->key, ws->nfirst, ws->ncount, ws->ngeo, ws->nlink,
                                              ws->nparent, ws->ctr, lst, (uint32_t)ws->p.leaf_cap,
-                                             (uint32_t)ws->node_cap, ws->dstatus);
+                                             (uint32_t)ws->node_cap, ws->dstatus, ws->dctl);
         maxl *= 8.0;
     }
     ws->launches += 1 + kLevels;
@@ -667,7 +678,9 @@ cudaError_t launch_octree(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
 template <typename Real>
 __global__ void __launch_bounds__(256) k_gather(const Real *__restrict__ x, const Real *__restrict__ m,
                                                 const uint32_t *__restrict__ idx, int64_t n,
-                                                typename Vec4<Real>::T *__restrict__ spos) {
+                                                typename Vec4<Real>::T *__restrict__ spos,
+                                                const uint32_t *__restrict__ ctr) {
+    if (aborted(ctr, kStageAfter)) return;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t i = idx[s];
         typename Vec4<Real>::T p;
@@ -683,7 +696,9 @@ __global__ void __launch_bounds__(256) k_gather(const Real *__restrict__ x, cons
 // vector load per particle.
 template <typename V4>
 __global__ void __launch_bounds__(256) k_gather_packed(const V4 *__restrict__ xm, const uint32_t *__restrict__ idx,
-                                                       int64_t n, V4 *__restrict__ spos) {
+                                                       int64_t n, V4 *__restrict__ spos,
+                                                       const uint32_t *__restrict__ ctr) {
+    if (aborted(ctr, kStageAfter)) return;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
         spos[s] = xm[idx[s]];
 }
@@ -691,9 +706,10 @@ __global__ void __launch_bounds__(256) k_gather_packed(const V4 *__restrict__ xm
 cudaError_t launch_gather_packed(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
     int nb = grid_for(n, 256, 152 * 16);
     if (ws->p.precision == TREE_F64)
-        k_gather_packed<double4a><<<nb, 256, 0, s>>>((const double4a *)ws->xm, ws->idx, n, (double4a *)ws->spos);
+        k_gather_packed<double4a><<<nb, 256, 0, s>>>((const double4a *)ws->xm, ws->idx, n, (double4a *)ws->spos,
+                                                     ws->ctr);
     else
-        k_gather_packed<float4><<<nb, 256, 0, s>>>((const float4 *)ws->xm, ws->idx, n, (float4 *)ws->spos);
+        k_gather_packed<float4><<<nb, 256, 0, s>>>((const float4 *)ws->xm, ws->idx, n, (float4 *)ws->spos, ws->ctr);
     ws->launches += 1;
     return cudaGetLastError();
 }
@@ -702,10 +718,10 @@ cudaError_t launch_gather(TreeWorkspace *ws, const void *x, const void *m, int64
     int nb = grid_for(n, 256, 152 * 16);
     if (ws->p.precision == TREE_F64)
         k_gather<double><<<nb, 256, 0, s>>>((const double *)x, (const double *)m, ws->idx, n,
-                                            (double4a *)ws->spos);
+                                            (double4a *)ws->spos, ws->ctr);
     else
         k_gather<float><<<nb, 256, 0, s>>>((const float *)x, (const float *)m, ws->idx, n,
-                                           (float4 *)ws->spos);
+                                           (float4 *)ws->spos, ws->ctr);
     ws->launches += 1;
     return cudaGetLastError();
 }

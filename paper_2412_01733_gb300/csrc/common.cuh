@@ -68,7 +68,24 @@ enum CounterSlots {
     kCtrGroups = kCtrLevelTrunc + 24,         // number of walk groups
     kCtrGScanTicket = kCtrGroups + 1,         // group-count scan tiles
     kCtrWalkTicket = kCtrGroups + 2,          // walk: next group slot (reset before every walk)
+    kCtrAbort = kCtrGroups + 3,               // stage whose bounded wait gave up (0: none)
     kCtrCount = kCtrGroups + 8
+};
+
+// Stages that wait on other blocks (decoupled look-backs).  When a wait of
+// stage S gives up, S is recorded in the counter block; the rest of S still
+// writes only in bounds, and every later kernel of the build (any other stage)
+// returns at once, so no kernel consumes the inconsistent data.
+constexpr uint32_t kStageSort0 = 1;        // sort pass p: 1 + p
+constexpr uint32_t kStageLevel0 = 16;      // octree level L: 16 + L
+constexpr uint32_t kStageGroupScan = 48;   // walk-group count scan
+constexpr uint32_t kStageAfter = 0xffffffffu;  // kernels that never wait
+
+// Device-side controls of the bounded waits (set from the host).
+struct DevCtl {
+    long long wait_cycles;  // give up after this many clock cycles
+    long long withhold;     // test injection: sort tile (pass << 32 | tile) that skips its look-back
+                            // publications, or -1
 };
 
 // Statistics slots (unsigned long long), cleared at the start of each walk.
@@ -112,6 +129,11 @@ struct TreeWorkspace {
     int seg_passes = 0;                // sort passes over the segment index (0, 1 or 2)
     int64_t chunks_cap = 0;            // capacity of ccount / coff
     int64_t box_cap = 1;               // DevBox entries allocated
+    // device copies of a host-resident state (leapfrog_step_host), allocated on first use
+    void *hs_x = nullptr, *hs_v = nullptr, *hs_m = nullptr, *hs_a = nullptr, *hs_phi = nullptr;
+    double *hs_diag = nullptr;
+    cudaStream_t copy_stream = nullptr;  // copies back that overlap the rest of the step
+    cudaEvent_t ev_drift = nullptr, ev_xback = nullptr;
     // one captured leapfrog step (leapfrog_graph_capture)
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
@@ -133,6 +155,7 @@ struct TreeWorkspace {
     void *mom_c = nullptr;             // Vec2: (Qxz, Qyz); FP32 copies hold -Q
     // status and statistics
     int32_t *dstatus = nullptr;
+    treegb::DevCtl *dctl = nullptr;    // bounded-wait controls
     unsigned long long *stats = nullptr;
     uint4 *gstat = nullptr;            // per walk group: {n_pc, n_pp particles, max stack, n_pp leaves}
     uint32_t *gfirst = nullptr;        // walk groups: first sorted index of each, then n
@@ -234,14 +257,38 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
     return v;
 }
 
+// What a bounded wait needs: where to report a timeout, the stage that waits,
+// and the limit.
+struct WaitCtx {
+    int32_t *dstatus;
+    uint32_t *ctr;         // counter block (kCtrAbort)
+    uint32_t stage;
+    long long limit;       // clock cycles
+};
+
+// True when a bounded wait of an earlier stage of this build gave up: the
+// calling kernel (of stage `stage`) must return without touching the data.
+__device__ __forceinline__ bool aborted(const uint32_t *ctr, uint32_t stage) {
+    const uint32_t a = ctr[kCtrAbort];
+    return a != 0u && a != stage;
+}
+
+__device__ __forceinline__ void wait_gave_up(const WaitCtx &w) {
+    set_status(w.dstatus, TREE_DEV_TIMEOUT);
+    atomicCAS(w.ctr + kCtrAbort, 0u, w.stage);
+}
+
 // Exclusive prefix of the tile after tile p from the look-back words of tiles
 // p, p-1, ... (word of tile q at st[q * stride]): adds aggregates back to the
 // first inclusive prefix.  Four predecessors are read at a time (independent
 // loads; flag and value share one word, so relaxed loads suffice), so a walk
 // over k tiles costs about k/4 load latencies; a word not yet published is
-// waited for (bounded: past kWaitCycles it sets TREE_DEV_TIMEOUT and ends the
-// walk).
-__device__ inline uint32_t lookback_walk(const uint32_t *st, size_t stride, int64_t p, int32_t *dstatus) {
+// waited for, bounded: past w.limit cycles the wait gives up (TREE_DEV_TIMEOUT,
+// the stage is recorded so that later kernels of the build return at once),
+// and the walk ends as if that word were an inclusive prefix of 0.  The
+// result then never exceeds the true prefix, so positions derived from it
+// stay in bounds.
+__device__ inline uint32_t lookback_walk(const uint32_t *st, size_t stride, int64_t p, const WaitCtx &wc) {
     uint32_t excl = 0;
     while (p >= 0) {
         uint32_t w[4];
@@ -253,8 +300,8 @@ __device__ inline uint32_t lookback_walk(const uint32_t *st, size_t stride, int6
             if ((v & ~kValMask) == 0) {
                 long long t0 = clock64();
                 while (((v = ld_relaxed(st + (size_t)(p - j) * stride)) & ~kValMask) == 0) {
-                    if (clock64() - t0 > kWaitCycles) {
-                        set_status(dstatus, TREE_DEV_TIMEOUT);
+                    if (clock64() - t0 > wc.limit) {
+                        wait_gave_up(wc);
                         v = kFlagInc;
                         break;
                     }
@@ -271,16 +318,14 @@ __device__ inline uint32_t lookback_walk(const uint32_t *st, size_t stride, int6
 
 // Single-value decoupled look-back: returns the exclusive prefix of tile
 // `tile` given its aggregate.  Call from one thread.  A wait that exceeds
-// kWaitCycles sets TREE_DEV_TIMEOUT and ends the look-back (the published
-// inclusive value is then wrong, but every waiter terminates).
-__device__ inline uint32_t lookback_single(uint32_t *status, uint32_t tile, uint32_t agg,
-                                           int32_t *dstatus) {
+// the limit gives up as in lookback_walk (every waiter terminates).
+__device__ inline uint32_t lookback_single(uint32_t *status, uint32_t tile, uint32_t agg, const WaitCtx &wc) {
     if (tile == 0) {
         st_release(status, kFlagInc | (agg & kValMask));
         return 0;
     }
     st_release(status + tile, kFlagAgg | (agg & kValMask));
-    const uint32_t excl = lookback_walk(status, 1, (int64_t)tile - 1, dstatus);
+    const uint32_t excl = lookback_walk(status, 1, (int64_t)tile - 1, wc);
     st_release(status + tile, kFlagInc | ((excl + agg) & kValMask));
     return excl;
 }
@@ -385,6 +430,8 @@ cudaError_t launch_adjoint(TreeWorkspace *ws, const void *abar, const void *phib
                            cudaStream_t s);
 cudaError_t launch_adjoint_step(TreeWorkspace *ws, void *xbar, void *vbar, void *abar, void *mbar,
                                 const void *phibar, double tau, cudaStream_t s);
+cudaError_t launch_energy_vjp(TreeWorkspace *ws, const void *m, const void *phi, const double *wbar, int64_t n,
+                              void *phibar, void *mbar, cudaStream_t s);
 // integrate.cu
 cudaError_t launch_kick_drift_box(TreeWorkspace *ws, void *x, void *v, const void *a, const void *m, double tau,
                                   int64_t n, cudaStream_t s);
@@ -395,6 +442,12 @@ cudaError_t launch_diagnostics_segments(TreeWorkspace *ws, const void *x, const 
 cudaError_t launch_direct(TreeWorkspace *ws, const void *x, const void *m, int64_t n, int dtype,
                           const int64_t *targets, int64_t nt, double *a_out, double *phi_out,
                           cudaStream_t s);
+cudaError_t launch_direct_range(TreeWorkspace *ws, const void *x, const void *m, int64_t n, int64_t jbeg,
+                                int64_t jend, int dtype, double G, double eps, const int64_t *targets, int64_t nt,
+                                double *a_out, double *phi_out, cudaStream_t s);
+cudaError_t launch_widen(TreeWorkspace *ws, const float *in, int64_t count, double *out, cudaStream_t s);
+cudaError_t launch_rel_err(TreeWorkspace *ws, const void *a, int64_t n, int dtype, const int64_t *tgt,
+                           const double *ref, int64_t nt, double *err, cudaStream_t s);
 cudaError_t launch_scan_lists(TreeWorkspace *ws, int64_t ngroups, cudaStream_t s);
 cudaError_t launch_gstat_reduce(TreeWorkspace *ws, int64_t ngroups, cudaStream_t s);
 cudaError_t launch_group_order(TreeWorkspace *ws, cudaStream_t s);

@@ -28,6 +28,7 @@ constexpr int kGScanTile = kGScanThreads * kGScanItems;
 __global__ void __launch_bounds__(256) k_leaf_levels(const uint32_t *__restrict__ ctr, const uint4 *__restrict__ ngeo,
                                                      const uint2 *__restrict__ nlink, uint8_t *__restrict__ plev,
                                                      uint32_t *__restrict__ pleaf) {
+    if (aborted(ctr, kStageAfter)) return;
     const uint32_t nn = ctr[kCtrLevelStart + kLevels];
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -103,6 +104,7 @@ __global__ void __launch_bounds__(256) k_group_chunks(const uint64_t *__restrict
                                                       uint32_t *__restrict__ ccount, const uint32_t *__restrict__ coff,
                                                       uint32_t *__restrict__ cmask, uint32_t *__restrict__ gfirst,
                                                       const uint32_t *__restrict__ ctr) {
+    if (aborted(ctr, kStageAfter)) return;
     const int lane = threadIdx.x & 31;
     const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (c >= nchunks) return;
@@ -137,8 +139,10 @@ __global__ void __launch_bounds__(256) k_group_chunks(const uint64_t *__restrict
 // the total is the group count.
 __global__ void __launch_bounds__(kGScanThreads) k_group_scan(const uint32_t *__restrict__ ccount,
                                                               uint32_t *__restrict__ coff, int64_t nchunks,
-                                                              uint32_t *status, uint32_t *ctr, int32_t *dstatus) {
+                                                              uint32_t *status, uint32_t *ctr, int32_t *dstatus,
+                                                              const DevCtl *__restrict__ ctl) {
     __shared__ uint32_t s_tile, s_excl, wt[32];
+    if (aborted(ctr, kStageGroupScan)) return;
     if (threadIdx.x == 0) s_tile = atomicAdd(ctr + kCtrGScanTicket, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
@@ -151,7 +155,8 @@ __global__ void __launch_bounds__(kGScanThreads) k_group_scan(const uint32_t *__
     }
     uint32_t tot;
     const uint32_t ex = block_exclusive_scan(sum, wt, &tot);
-    if (threadIdx.x == 0) s_excl = lookback_single(status, tile, tot, dstatus);
+    if (threadIdx.x == 0)
+        s_excl = lookback_single(status, tile, tot, WaitCtx{dstatus, ctr, kStageGroupScan, ctl->wait_cycles});
     __syncthreads();
     uint32_t run = s_excl + ex;
 #pragma unroll
@@ -176,7 +181,7 @@ cudaError_t launch_groups(TreeWorkspace *ws, int64_t n, cudaStream_t s) {
                                             ws->p.group_split, nchunks, ws->seg_off, ws->seg_cstart, ws->nseg, ws->ccount,
                                             nullptr, ws->cmask, nullptr, ws->ctr);
     k_group_scan<<<(unsigned)tiles, kGScanThreads, 0, s>>>(ws->ccount, ws->coff, nchunks, ws->gscan_status, ws->ctr,
-                                                          ws->dstatus);
+                                                          ws->dstatus, ws->dctl);
     k_group_chunks<true><<<wb, 256, 0, s>>>(ws->key, ws->plev, ws->pleaf, ws->nparent, ws->ncount, cmax, n, gs,
                                            ws->p.group_split, nchunks, ws->seg_off, ws->seg_cstart, ws->nseg, nullptr,
                                            ws->coff, ws->cmask, ws->gfirst, ws->ctr);

@@ -228,24 +228,28 @@ cudaError_t launch_diagnostics_segments(TreeWorkspace *ws, const void *x, const 
 }
 
 // ============================================================== direct sum (Eq. 1)
-// blockIdx.x: 128 targets; blockIdx.y: one chunk of sources.  FP32: pair terms
-// in FP32, per-128-source partial sums folded with Kahan compensation; the
-// chunk totals are written in FP64 and summed over chunks in a fixed order.
+// blockIdx.x: 128 targets; blockIdx.y: one chunk of the sources [jbeg, jend).
+// Pair terms in the working precision through the reciprocal square root;
+// per-128-source partial sums folded with Kahan compensation; the chunk totals
+// are written in FP64 and summed over chunks in a fixed order.  A target index
+// outside [0, n) reads nothing and gets NaN results.
 constexpr int kDirThreads = 128;
 
 template <typename Real>
 __global__ void __launch_bounds__(kDirThreads) k_direct(const Real *__restrict__ x, const Real *__restrict__ m,
-                                                        int64_t n, const int64_t *__restrict__ tgt, int64_t nt,
-                                                        int64_t chunk, double eps2d, double *__restrict__ part) {
+                                                        int64_t n, int64_t jbeg, int64_t jend,
+                                                        const int64_t *__restrict__ tgt, int64_t nt, int64_t chunk,
+                                                        double eps2d, double *__restrict__ part) {
     using V4 = typename Vec4<Real>::T;
     __shared__ V4 src[kDirThreads];
     const int64_t t = blockIdx.x * (int64_t)kDirThreads + threadIdx.x;
     const int64_t ti = t < nt ? tgt[t] : -1;
+    const bool valid = ti >= 0 && ti < n;
     Real px = 0, py = 0, pz = 0;
-    if (ti >= 0) { px = x[ti]; py = x[n + ti]; pz = x[2 * n + ti]; }
+    if (valid) { px = x[ti]; py = x[n + ti]; pz = x[2 * n + ti]; }
     const Real eps2 = (Real)eps2d;
-    const int64_t j0 = blockIdx.y * chunk;
-    const int64_t j1 = min(n, j0 + chunk);
+    const int64_t j0 = jbeg + blockIdx.y * chunk;
+    const int64_t j1 = min(jend, j0 + chunk);
     Real sum[4] = {0, 0, 0, 0}, cmp[4] = {0, 0, 0, 0};
     for (int64_t jb = j0; jb < j1; jb += kDirThreads) {
         const int64_t j = jb + threadIdx.x;
@@ -263,10 +267,11 @@ __global__ void __launch_bounds__(kDirThreads) k_direct(const Real *__restrict__
             const Real dx = q.x - px, dy = q.y - py, dz = q.z - pz;
             const Real r2 = dx * dx + dy * dy + dz * dz + eps2;
             if (!(r2 > Real(0))) continue;
-            const Real r = sqrt(r2);
-            const Real w = q.w / (r2 * r);
+            const Real ri = sizeof(Real) == 8 ? (Real)rsqrt((double)r2) : (Real)rsqrtf((float)r2);
+            const Real mr = q.w * ri;
+            const Real w = mr * (ri * ri);
             part_[0] += w * dx; part_[1] += w * dy; part_[2] += w * dz;
-            part_[3] -= q.w / r;
+            part_[3] -= mr;
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -279,7 +284,7 @@ __global__ void __launch_bounds__(kDirThreads) k_direct(const Real *__restrict__
     if (t < nt) {
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            part[((int64_t)blockIdx.y * 4 + c) * nt + t] = (double)sum[c] - (double)cmp[c];
+            part[((int64_t)blockIdx.y * 4 + c) * nt + t] = valid ? (double)sum[c] - (double)cmp[c] : (double)NAN;
     }
 }
 
@@ -296,19 +301,31 @@ __global__ void k_direct_final(const double *__restrict__ part, int64_t nt, int 
     if (phi_out) phi_out[t] = G * r[3];
 }
 
-cudaError_t launch_direct(TreeWorkspace *ws, const void *x, const void *m, int64_t n, int dtype,
-                          const int64_t *targets, int64_t nt, double *a_out, double *phi_out,
-                          cudaStream_t s) {
+// Chunking of the sources [jbeg, jend) for nt targets: about 16 blocks per SM
+// in all, chunks a multiple of the block's 128 sources, at most max_chunks.
+static void direct_chunks(int64_t nsrc, int64_t nt, int64_t max_chunks, int64_t *chunk_out, int64_t *nch_out) {
     const int64_t tt = (nt + kDirThreads - 1) / kDirThreads;
     int64_t nch = (152 * 16 + tt - 1) / tt;
-    int64_t maxch = (n + kDirThreads - 1) / kDirThreads;
+    const int64_t maxch = (nsrc + kDirThreads - 1) / kDirThreads;
     if (nch > maxch) nch = maxch;
-    if (nch < 1) nch = 1;
+    if (nch > max_chunks) nch = max_chunks;
     if (nch > 65535) nch = 65535;
-    int64_t chunk = (n + nch - 1) / nch;
-    chunk = ((chunk + kDirThreads - 1) / kDirThreads) * kDirThreads;
-    nch = (n + chunk - 1) / chunk;
     if (nch < 1) nch = 1;
+    int64_t chunk = (nsrc + nch - 1) / nch;
+    chunk = ((chunk + kDirThreads - 1) / kDirThreads) * kDirThreads;
+    if (chunk < kDirThreads) chunk = kDirThreads;
+    nch = (nsrc + chunk - 1) / chunk;
+    if (nch < 1) nch = 1;
+    *chunk_out = chunk;
+    *nch_out = nch;
+}
+
+// Direct sum for nt targets over the sources [jbeg, jend) of x (stride n).
+cudaError_t launch_direct_range(TreeWorkspace *ws, const void *x, const void *m, int64_t n, int64_t jbeg,
+                                int64_t jend, int dtype, double G, double eps, const int64_t *targets, int64_t nt,
+                                double *a_out, double *phi_out, cudaStream_t s) {
+    int64_t chunk = 0, nch = 1;
+    direct_chunks(jend - jbeg, nt, INT64_MAX, &chunk, &nch);
     const size_t need = (size_t)nch * 4 * (size_t)nt * sizeof(double);
     if (need > ws->direct_part_bytes) {
         if (ws->direct_part) cudaFree(ws->direct_part);
@@ -318,17 +335,64 @@ cudaError_t launch_direct(TreeWorkspace *ws, const void *x, const void *m, int64
         if (e != cudaSuccess) return e;
         ws->direct_part_bytes = need;
     }
+    const int64_t tt = (nt + kDirThreads - 1) / kDirThreads;
     dim3 grid((unsigned)tt, (unsigned)nch);
-    const double eps2 = ws->p.eps * ws->p.eps;
+    const double eps2 = eps * eps;
     if (dtype == TREE_F64)
-        k_direct<double><<<grid, kDirThreads, 0, s>>>((const double *)x, (const double *)m, n, targets, nt, chunk,
-                                                      eps2, ws->direct_part);
+        k_direct<double><<<grid, kDirThreads, 0, s>>>((const double *)x, (const double *)m, n, jbeg, jend, targets,
+                                                      nt, chunk, eps2, ws->direct_part);
     else
-        k_direct<float><<<grid, kDirThreads, 0, s>>>((const float *)x, (const float *)m, n, targets, nt, chunk,
-                                                     eps2, ws->direct_part);
-    k_direct_final<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(ws->direct_part, nt, (int)nch, ws->p.G, a_out,
-                                                                phi_out);
+        k_direct<float><<<grid, kDirThreads, 0, s>>>((const float *)x, (const float *)m, n, jbeg, jend, targets, nt,
+                                                     chunk, eps2, ws->direct_part);
+    k_direct_final<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(ws->direct_part, nt, (int)nch, G, a_out, phi_out);
     ws->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_direct(TreeWorkspace *ws, const void *x, const void *m, int64_t n, int dtype,
+                          const int64_t *targets, int64_t nt, double *a_out, double *phi_out,
+                          cudaStream_t s) {
+    return launch_direct_range(ws, x, m, n, 0, n, dtype, ws->p.G, ws->p.eps, targets, nt, a_out, phi_out, s);
+}
+
+// Widen FP32 positions / masses to FP64 (exact).
+__global__ void k_widen(const float *__restrict__ in, int64_t count, double *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+cudaError_t launch_widen(TreeWorkspace *ws, const float *in, int64_t count, double *out, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    k_widen<<<grid_for(count, 256, 152 * 8), 256, 0, s>>>(in, count, out);
+    ws->launches += 1;
+    return cudaGetLastError();
+}
+
+// err[t] = |a[:, tgt[t]] - ref[:, t]| / |ref[:, t]| (a: [3][n] of Real, ref: [3][nt] FP64).
+template <typename Real>
+__global__ void k_rel_err(const Real *__restrict__ a, int64_t n, const int64_t *__restrict__ tgt,
+                          const double *__restrict__ ref, int64_t nt, double *__restrict__ err) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const int64_t i = tgt[t];
+    double d2 = 0.0, r2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        const double r = ref[c * nt + t];
+        const double d = (double)a[c * n + i] - r;
+        d2 += d * d;
+        r2 += r * r;
+    }
+    err[t] = r2 > 0.0 ? sqrt(d2 / r2) : (d2 > 0.0 ? (double)INFINITY : 0.0);
+}
+
+cudaError_t launch_rel_err(TreeWorkspace *ws, const void *a, int64_t n, int dtype, const int64_t *tgt,
+                           const double *ref, int64_t nt, double *err, cudaStream_t s) {
+    if (nt <= 0) return cudaSuccess;
+    if (dtype == TREE_F64)
+        k_rel_err<double><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>((const double *)a, n, tgt, ref, nt, err);
+    else
+        k_rel_err<float><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>((const float *)a, n, tgt, ref, nt, err);
+    ws->launches += 1;
     return cudaGetLastError();
 }
 
@@ -551,28 +615,21 @@ extern "C" tree_status_t tree_direct_forces_noalloc(const void *x, const void *m
     double *part = nullptr;
     if (noalloc_scratch(&part) != cudaSuccess) return TREE_ERR_CUDA;
     // same chunking as tree_direct_forces, capped so the partials fit the array
-    const int64_t tt = (nt + kDirThreads - 1) / kDirThreads;
-    int64_t nch = (152 * 16 + tt - 1) / tt;
-    const int64_t maxch = (n + kDirThreads - 1) / kDirThreads;
     const int64_t fit = kNoAllocScratchDoubles / (4 * nt);
-    if (nch > maxch) nch = maxch;
-    if (nch > fit) nch = fit;
-    if (nch < 1) nch = 1;
-    int64_t chunk = (n + nch - 1) / nch;
-    chunk = ((chunk + kDirThreads - 1) / kDirThreads) * kDirThreads;
-    nch = (n + chunk - 1) / chunk;
-    if (nch < 1) nch = 1;
+    int64_t chunk = 0, nch = 1;
+    direct_chunks(n, nt, fit, &chunk, &nch);
     // every partial slot [chunk][component][target] is written exactly once
     // before it is read, so the array needs no clearing between calls
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t tt = (nt + kDirThreads - 1) / kDirThreads;
     dim3 grid((unsigned)tt, (unsigned)nch);
     const double eps2 = eps * eps;
     if (dtype == TREE_F64)
-        k_direct<double><<<grid, kDirThreads, 0, s>>>((const double *)x, (const double *)m, n, targets, nt, chunk,
-                                                      eps2, part);
+        k_direct<double><<<grid, kDirThreads, 0, s>>>((const double *)x, (const double *)m, n, 0, n, targets, nt,
+                                                      chunk, eps2, part);
     else
-        k_direct<float><<<grid, kDirThreads, 0, s>>>((const float *)x, (const float *)m, n, targets, nt, chunk, eps2,
-                                                     part);
+        k_direct<float><<<grid, kDirThreads, 0, s>>>((const float *)x, (const float *)m, n, 0, n, targets, nt, chunk,
+                                                     eps2, part);
     k_direct_final<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(part, nt, (int)nch, G, a_out, phi_out);
     return cudaGetLastError() == cudaSuccess ? TREE_OK : TREE_ERR_CUDA;
 }

@@ -35,6 +35,8 @@ __device__ __forceinline__ uint32_t mom_bucket(uint4 g, uint2 l) {
 // Bucket counts of all nodes.
 __global__ void __launch_bounds__(256) k_mom_hist(const uint32_t *__restrict__ ctr, const uint4 *__restrict__ ngeo,
                                                   const uint2 *__restrict__ nlink, uint32_t *__restrict__ cnt) {
+    // after a given-up wait the buckets stay empty, so no later moment kernel does any work
+    if (aborted(ctr, kStageAfter)) return;
     __shared__ uint32_t sh[kMomBuckets];
     for (int i = threadIdx.x; i < kMomBuckets; i += blockDim.x) sh[i] = 0;
     __syncthreads();
@@ -53,6 +55,7 @@ __global__ void __launch_bounds__(256) k_mom_scatter(const uint32_t *__restrict_
                                                      const uint2 *__restrict__ nlink, const uint32_t *__restrict__ cnt,
                                                      uint32_t *__restrict__ off, uint32_t *__restrict__ cursor,
                                                      uint32_t *__restrict__ order) {
+    if (aborted(ctr, kStageAfter)) return;
     __shared__ uint32_t s_off[kMomBuckets + 1], s_cnt[kMomBuckets], s_base[kMomBuckets];
     for (int b = threadIdx.x; b < kMomBuckets; b += blockDim.x) s_cnt[b] = cnt[b];
     __syncthreads();

@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
     using V2 = typename Vec2<Real>::T;
     extern __shared__ __align__(32) unsigned char smem[];
     __shared__ long long sD[kLevels];
+    if (aborted(A.ctr, kStageAfter)) return;  // the build gave up a wait: no valid tree
     if (threadIdx.x < kLevels) sD[threadIdx.x] = A.dmac[threadIdx.x];
     __syncthreads();
 

@@ -101,12 +101,14 @@ def plummer(n: int, seed: int = DEFAULT_SEED, *, a: float = 1.0, M: float = 1.0,
 
 def galaxy(n: int, seed: int = DEFAULT_SEED, *, f_disk=0.6, f_bulge=0.1, Rd=1.0,
            z0=0.1, a_b=0.2, rs=5.0, rt=50.0, M=1.0, G=1.0, sigma_frac=0.1,
-           device="cpu", dtype=torch.float64, shuffle: bool = True):
+           device="cpu", dtype=torch.float64, shuffle: bool = True, return_component: bool = False):
     """Galaxy-like model: exponential disc + Hernquist bulge + truncated NFW halo.
 
     Component masses f_disk M, f_bulge M, (1 - f_disk - f_bulge) M; particle
     counts in the same proportions, so particle masses are equal within a
     component.  Output order is a random permutation of the particles.
+    return_component: also return each particle's component (int8: 0 disc,
+    1 bulge, 2 halo), in the same order.
     """
     n = int(n)
     g = _gen(seed, device)
@@ -182,9 +184,14 @@ def galaxy(n: int, seed: int = DEFAULT_SEED, *, f_disk=0.6, f_bulge=0.1, Rd=1.0,
     m = torch.cat((torch.full((n_d,), f_disk * M / max(n_d, 1), **f64),
                    torch.full((n_b,), f_bulge * M / max(n_b, 1), **f64),
                    torch.full((n_h,), f_halo * M / max(n_h, 1), **f64)))
+    comp = torch.cat((torch.zeros(n_d, dtype=torch.int8, device=device),
+                      torch.ones(n_b, dtype=torch.int8, device=device),
+                      torch.full((n_h,), 2, dtype=torch.int8, device=device)))
     if shuffle and n > 1:
         p = torch.randperm(n, generator=g, device=device)
-        x, v, m = x[:, p], v[:, p], m[p]
+        x, v, m, comp = x[:, p], v[:, p], m[p], comp[p]
+    if return_component:
+        return x.to(dtype), v.to(dtype), m.to(dtype), comp
     return x.to(dtype), v.to(dtype), m.to(dtype)
 
 

@@ -21,7 +21,8 @@ DEV_NONFINITE, DEV_STACK, DEV_NODES, DEV_TIMEOUT, DEV_LIST = 0x01, 0x02, 0x04, 0
 F32, F64 = 0, 1
 FLAG_EMIT_LISTS = 0x1
 FLAG_LISTS_ONLY = 0x2
-PHASES = ("box", "keys", "sort", "octree", "gather", "moments", "walk", "lists", "diag", "direct", "adjoint")
+PHASES = ("box", "keys", "sort", "octree", "gather", "moments", "walk", "lists", "diag", "direct", "adjoint",
+          "h2d", "d2h")
 
 
 class TreeParams(ctypes.Structure):
@@ -60,15 +61,20 @@ _SIGNATURES = {
     "tree_forces": [_vp, _vp, _vp, _i32, _vp],
     "tree_accel": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "tree_forces_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "tree_energy_vjp": [_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "leapfrog_adjoint_step": [_vp, _vp, _vp, _vp, _vp, _vp, _dbl, _vp],
     "leapfrog_step": [_vp, _vp, _vp, _vp, _vp, _vp, _dbl, _i64, _vp],
+    "leapfrog_step_host": [_vp, _vp, _vp, _vp, _vp, _vp, _dbl, _i64, _vp, _vp],
     "tree_diagnostics": [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp],
     "tree_direct_forces": [_vp, _vp, _vp, _i64, _i32, _vp, _i64, _vp, _vp, _vp],
     "tree_get_status": [_vp, ctypes.POINTER(_i32), _i32],
+    "tree_set_waits": [_vp, _i64, _i32, _i64],
     "tree_get_info": [_vp, ctypes.POINTER(TreeInfo)],
     "tree_export_tree": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "tree_export_moments": [_vp, _vp, _vp, _vp, _vp],
     "tree_export_lists": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "tree_export_lists_groups": [_vp, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _vp,
+                                 ctypes.POINTER(_i64), _vp, _vp],
     "tree_export_group_stats": [_vp, _vp, _vp],
     "tree_export_groups": [_vp, _vp, _vp],
     "tree_mac_table": [_dbl, ctypes.POINTER(_i64)],
@@ -80,9 +86,10 @@ _SIGNATURES = {
     "tree_diagnostics_segments": [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp],
     "leapfrog_graph_capture": [_vp, _vp, _vp, _vp, _vp, _vp, _dbl, _i64, _vp],
     "leapfrog_graph_launch": [_vp, _vp],
-    "tree_autotune": [ctypes.POINTER(TreeParams), _i64, ctypes.POINTER(_i64), _vp, _vp, _i64, _i32,
+    "tree_autotune": [ctypes.POINTER(TreeParams), _i64, ctypes.POINTER(_i64), _vp, _vp, _i64, _i32, _dbl,
                       ctypes.POINTER(TreeParams), ctypes.POINTER(_dbl), ctypes.POINTER(_i32), _vp],
     "tree_export_boxes": [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i32)],
+    "tree_fp32_peak": [ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)],
     "tree_status_string": [_i32],
     "tree_version": [],
 }
@@ -124,6 +131,13 @@ def mac_table(theta: float):
     return [int(v) for v in D]
 
 
+def fp32_peak():
+    """Measured FP32 FMA throughput of the current GPU, (scalar, packed) in TFLOP/s."""
+    a, b = _dbl(0.0), _dbl(0.0)
+    _check("tree_fp32_peak", lib().tree_fp32_peak(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 def default_params(**kw) -> TreeParams:
     p = TreeParams()
     _check("tree_params_default", lib().tree_params_default(ctypes.byref(p)))
@@ -140,10 +154,12 @@ def _offsets(offsets):
     return len(offs) - 1, arr
 
 
-def autotune(x, m, offsets=None, reps=3, **params):
+def autotune(x, m, offsets=None, reps=3, max_err=1e-3, **params):
     """Fastest (leaf_cap, group_size, stack_depth) for one force evaluation of (x, m)
-    (ensemble: offsets as in Workspace.set_segments).  Returns (TreeParams, table)
-    with table rows (leaf_cap, group_size, stack_depth, ms)."""
+    (ensemble: offsets as in Workspace.set_segments) among the candidates whose median
+    relative force error against the FP64 direct sum on a fixed sample is <= max_err
+    (None or <= 0: no bound).  Returns (TreeParams, table) with table rows
+    (leaf_cap, group_size, stack_depth, ms, median error)."""
     base = default_params(**params)
     dt = torch.float64 if base.precision == F64 else torch.float32
     n = x.shape[1]
@@ -154,11 +170,12 @@ def autotune(x, m, offsets=None, reps=3, **params):
     nseg, arr = _offsets(offsets) if offsets is not None else (0, None)
     best = TreeParams()
     rows = 32
-    table = (_dbl * (4 * rows))()
+    table = (_dbl * (5 * rows))()
     nc = _i32(rows)
+    bound = 0.0 if max_err is None else float(max_err)
     _check("tree_autotune", lib().tree_autotune(ctypes.byref(base), nseg, arr, _ptr(x), _ptr(m), n, int(reps),
-                                                ctypes.byref(best), table, ctypes.byref(nc), _stream()))
-    tab = [tuple(table[4 * i + k] for k in range(4)) for i in range(min(nc.value, rows))]
+                                                bound, ctypes.byref(best), table, ctypes.byref(nc), _stream()))
+    tab = [tuple(table[5 * i + k] for k in range(5)) for i in range(min(nc.value, rows))]
     return best, tab
 
 
@@ -326,6 +343,20 @@ class Workspace:
                                                                 _ptr(m_bar), _stream()))
         return x_bar, m_bar
 
+    def energy_vjp(self, m, phi, w_bar, phi_bar=None, m_bar=None):
+        """Cotangents of W = 1/2 sum m phi (tree_energy_vjp): w_bar a CUDA float64 tensor of one
+        element; returns phi_bar (w_bar m / 2, allocated if None) after adding w_bar phi / 2 to m_bar."""
+        n = m.shape[0]
+        self._scal(m, n, "m"); self._scal(phi, n, "phi")
+        if not w_bar.is_cuda or w_bar.dtype != torch.float64 or w_bar.numel() != 1:
+            raise ValueError("w_bar must be a CUDA float64 tensor of one element")
+        if phi_bar is None:
+            phi_bar = torch.empty_like(m)
+        self._scal(phi_bar, n, "phi_bar"); self._scal(m_bar, n, "m_bar", optional=True)
+        _check("tree_energy_vjp", lib().tree_energy_vjp(self._h, _ptr(m), _ptr(phi), _ptr(w_bar.contiguous()), n,
+                                                        _ptr(phi_bar), _ptr(m_bar), _stream()))
+        return phi_bar
+
     def leapfrog_adjoint_step(self, x_bar, v_bar, a_bar, m_bar, tau, phi_bar=None):
         """One reverse leapfrog step through the tree stored at x_{n+1} (see treegb.h); in place."""
         n = self.n
@@ -358,6 +389,22 @@ class Workspace:
                                                     float(tau), n, _stream()))
         self.n = n
 
+    def leapfrog_step_host(self, x, v, m, a, tau, phi=None, diag=None):
+        """One KDK step on a host-resident state (leapfrog_step_host): x, v, a (3, n), m, phi (n,) and
+        diag (8,) float64 are pinned CPU tensors, updated when the current stream has run."""
+        n = x.shape[1]
+        for t, nm, shape in ((x, "x", (3, n)), (v, "v", (3, n)), (a, "a", (3, n)), (m, "m", (n,)),
+                             (phi, "phi", (n,))):
+            if t is None and nm == "phi":
+                continue
+            if t.is_cuda or t.dtype != self.dtype or tuple(t.shape) != shape or not t.is_contiguous():
+                raise ValueError(f"{nm} must be a contiguous host {self.dtype} tensor of shape {shape}")
+        if diag is not None and (diag.is_cuda or diag.dtype != torch.float64 or diag.numel() < 8):
+            raise ValueError("diag must be a host float64 tensor of 8")
+        _check("leapfrog_step_host", lib().leapfrog_step_host(self._h, _ptr(x), _ptr(v), _ptr(m), _ptr(a), _ptr(phi),
+                                                              float(tau), n, _ptr(diag), _stream()))
+        self.n = n
+
     def diagnostics(self, x, v, m, phi=None, out=None):
         """FP64 (E_kin, W, Px, Py, Pz, Lx, Ly, Lz) as a CUDA float64 tensor of 8."""
         n = x.shape[1]
@@ -386,6 +433,12 @@ class Workspace:
                                                               n, dt, _ptr(targets), nt, _ptr(a), _ptr(phi),
                                                               _stream()))
         return a, phi
+
+    def set_waits(self, wait_cycles=0, withhold=None):
+        """Limit of the device-side waits in clock cycles (0: keep), and the test injection
+        withhold = (sort pass, tile) whose look-back words stay unpublished (None: off)."""
+        wp, wt = (-1, -1) if withhold is None else (int(withhold[0]), int(withhold[1]))
+        _check("tree_set_waits", lib().tree_set_waits(self._h, int(wait_cycles), wp, wt))
 
     # -- state, statistics, exports -----------------------------------------
     def status(self, clear=True) -> int:
@@ -471,3 +524,19 @@ class Workspace:
         _check("tree_export_lists", lib().tree_export_lists(self._h, _ptr(pc_off), _ptr(pc), _ptr(pp_off),
                                                             _ptr(pp), _stream()))
         return pc_off, pc[: inf["list_pc"]], pp_off, pp[: inf["list_pp"]]
+
+    def export_lists_groups(self, gsel):
+        """Lists of the selected groups (tree_export_lists_groups): (pc_off, pc, pp_off, pp) with the
+        offsets as host int64 lists of len(gsel) + 1 and the entries as int32 CUDA tensors."""
+        gs = [int(g) for g in gsel]
+        k = len(gs)
+        sel = (_i64 * max(k, 1))(*gs)
+        pco = (_i64 * (k + 1))()
+        ppo = (_i64 * (k + 1))()
+        _check("tree_export_lists_groups", lib().tree_export_lists_groups(self._h, k, sel, pco, None, ppo, None,
+                                                                          _stream()))
+        pc = torch.empty(max(1, pco[k]), dtype=torch.int32, device="cuda")
+        pp = torch.empty(max(1, ppo[k]), dtype=torch.int32, device="cuda")
+        _check("tree_export_lists_groups", lib().tree_export_lists_groups(self._h, k, sel, pco, _ptr(pc), ppo,
+                                                                          _ptr(pp), _stream()))
+        return list(pco), pc[: pco[k]], list(ppo), pp[: ppo[k]]

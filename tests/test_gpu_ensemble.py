@@ -189,10 +189,39 @@ def test_autotune_picks_fastest_valid():
     best, table = tg.autotune(x.contiguous(), m.contiguous(), offsets=off, reps=2, **P)
     assert len(table) == 18
     ms = np.array([r[3] for r in table])
+    err = np.array([r[4] for r in table])
     assert np.isfinite(ms).any()
+    # every candidate meets the default bound (median error <= 1e-3) at theta = 0.6
+    assert np.all(err[np.isfinite(ms)] <= 1e-3) and np.all(err > 0)
     i = int(np.nanargmin(np.where(np.isfinite(ms), ms, np.inf)))
     assert (best.leaf_cap, best.group_size, best.stack_depth) == tuple(int(t) for t in table[i][:3])
     assert best.theta == P["theta"] and best.eps == P["eps"]
+
+
+def test_autotune_error_bound_excludes_fastest():
+    """With a bound just below the error of the fastest candidate, the tuner must
+    return a slower candidate that meets it: the fastest one among those whose
+    median force error against the FP64 direct sum is within the bound."""
+    tg = _tg()
+    x, v, m, off = inputs.ensemble(16, 5, nmin=512, nmax=8192, device="cuda", dtype=torch.float32)
+    x, m = x.contiguous(), m.contiguous()
+    _, free = tg.autotune(x, m, offsets=off, reps=2, max_err=None, **P)
+    ms = np.array([r[3] for r in free]); err = np.array([r[4] for r in free])
+    i0 = int(np.argmin(ms))
+    assert np.isfinite(ms[i0])
+    bound = 0.999 * err[i0]
+    assert (err <= bound).any(), "some candidate is more accurate than the fastest one"
+    best, tab = tg.autotune(x, m, offsets=off, reps=2, max_err=bound, **P)
+    ms2 = np.array([r[3] for r in tab]); err2 = np.array([r[4] for r in tab])
+    np.testing.assert_array_equal(err2, err)             # the error column does not depend on timing
+    assert not np.isfinite(ms2[err2 > bound]).any()      # every candidate above the bound is rejected
+    j = [tuple(int(t) for t in r[:3]) for r in tab].index((best.leaf_cap, best.group_size, best.stack_depth))
+    assert err2[j] <= bound and ms2[j] == np.min(ms2[np.isfinite(ms2)])
+    assert tuple(int(t) for t in tab[j][:3]) != tuple(int(t) for t in free[i0][:3])
+    # a bound below every candidate's error leaves none
+    with pytest.raises(tg.TreeError) as e:
+        tg.autotune(x, m, offsets=off, reps=1, max_err=0.5 * err.min(), **P)
+    assert e.value.code == tg.TREE_ERR_DEVICE
 
 
 def test_ensemble_adjoint_equals_alone():

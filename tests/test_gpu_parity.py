@@ -46,10 +46,11 @@ def _rel_err(a, ref):
 
 
 def _segment_sorted(off, vals):
+    """Entries of each CSR segment in ascending order (segments kept in place)."""
     off = np.asarray(off, np.int64)
-    g = np.repeat(np.arange(len(off) - 1), np.diff(off))
-    order = np.lexsort((np.asarray(vals, np.int64), g))
-    return np.asarray(vals, np.int64)[order]
+    g = np.repeat(np.arange(len(off) - 1, dtype=np.int64), np.diff(off))
+    key = (g << 32) | np.asarray(vals, np.int64)
+    return np.sort(key) & 0xffffffff
 
 
 def _check_structure(orc, ws, xg, mg, ref, gs):
@@ -374,3 +375,22 @@ def test_diagnostics_match_oracle(orc):
     np.testing.assert_allclose(d[1], do["epot"], rtol=1e-13)
     np.testing.assert_allclose(d[2:5], do["P"], atol=1e-15)
     np.testing.assert_allclose(d[5:8], do["L"], atol=1e-14)
+
+
+def test_export_lists_groups_matches_full_export():
+    """tree_export_lists_groups gives, for any selection of groups (any order,
+    repeats allowed), exactly the segments of the full list export."""
+    tg = _tg()
+    x, m = _gen("galaxy", 30000)
+    ws, xg, mg, a, phi = _run(x, m, eps=0.02, theta=0.7, order=2, leaf_cap=16, group_size=32)
+    pc_off, pc, pp_off, pp = (v.cpu().numpy() for v in ws.export_lists())
+    ng = len(pc_off) - 1
+    sel = [ng - 1, 0, 17, 17, ng // 2, 3]
+    so, spc, po, spp = ws.export_lists_groups(sel)
+    spc, spp = spc.cpu().numpy(), spp.cpu().numpy()
+    for k, g in enumerate(sel):
+        np.testing.assert_array_equal(spc[so[k]: so[k + 1]], pc[pc_off[g]: pc_off[g + 1]])
+        np.testing.assert_array_equal(spp[po[k]: po[k + 1]], pp[pp_off[g]: pp_off[g + 1]])
+    with pytest.raises(tg.TreeError) as e:
+        ws.export_lists_groups([ng])
+    assert e.value.code == tg.TREE_ERR_ARG

@@ -38,8 +38,8 @@ def _noalloc(tg, x, m, targets, precision, G, eps):
     return a, phi
 
 
-@pytest.mark.parametrize("precision,rtol", [("f32", 1e-6), ("f64", 1e-12)])
-def test_noalloc_matches_workspace_direct(precision, rtol):
+@pytest.mark.parametrize("precision,rtol,rtol_orc", [("f32", 1e-6, 1e-5), ("f64", 1e-12, 1e-12)])
+def test_noalloc_matches_workspace_direct(orc, precision, rtol, rtol_orc):
     tg = _lib()
     dt = torch.float64 if precision == "f64" else torch.float32
     n = 30000
@@ -58,6 +58,13 @@ def test_noalloc_matches_workspace_direct(precision, rtol):
         ea = ((a1 - a0).norm(dim=0) / a0.norm(dim=0)).max().item()
         ep = ((p1 - p0).abs() / p0.abs()).max().item()
         assert ea <= rtol and ep <= rtol, (call, ea, ep)
+        # and the FP64 oracle's direct sum of Eq. 1 on the same inputs (first 300 targets)
+        t3 = tgt[:300].cpu().numpy()
+        ao, po = orc.direct(x.double().cpu().numpy(), m.double().cpu().numpy(), G=G, eps=eps, targets=t3)
+        a1n, p1n = a1[:, :300].cpu().numpy(), p1[:300].cpu().numpy()
+        eo = (np.linalg.norm(a1n - ao, axis=0) / np.linalg.norm(ao, axis=0)).max()
+        epo = (np.abs(p1n - po) / np.abs(po)).max()
+        assert eo <= rtol_orc and epo <= rtol_orc, (call, eo, epo)
 
 
 def test_noalloc_rejects_too_many_targets():
@@ -71,3 +78,18 @@ def test_noalloc_rejects_too_many_targets():
         ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(m.data_ptr()), 10, tg.F32, 1.0, 0.01,
         ctypes.c_void_p(tgt.data_ptr()), 4097, ctypes.c_void_p(out.data_ptr()), None, None)
     assert code == tg.TREE_ERR_CAPACITY
+
+
+def test_noalloc_target_out_of_range_gives_nan():
+    """A target index outside [0, n) reads nothing and yields NaN for that
+    target only."""
+    tg = _lib()
+    x, _, m = inputs.plummer(500, 4)
+    x = x.to("cuda", torch.float32).contiguous()
+    m = m.to("cuda", torch.float32).contiguous()
+    tgt = torch.tensor([-1, 500, 3, 1 << 40], dtype=torch.int64, device="cuda")
+    a, phi = _noalloc(tg, x, m, tgt, "f32", 1.0, 0.01)
+    torch.cuda.synchronize()
+    bad = torch.tensor([True, True, False, True], device="cuda")
+    assert torch.isnan(a[:, bad]).all() and torch.isnan(phi[bad]).all()
+    assert torch.isfinite(a[:, 2]).all() and torch.isfinite(phi[2])
