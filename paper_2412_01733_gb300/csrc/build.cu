@@ -419,11 +419,11 @@ __global__ void __launch_bounds__(kSortThreads, MODE == kPassSeg ? 2 : 3) k_ones
         // after it run into their wait limit
         const bool publish = ctl->withhold != (((long long)pass << 32) | (long long)tile);
         if (tile == 0) {
-            if (publish) st_release(st, kFlagInc | tcount);
+            if (publish) st_publish(st, kFlagInc | tcount);
         } else {
-            if (publish) st_release(st + (size_t)tile * kRadix, kFlagAgg | tcount);
+            if (publish) st_publish(st + (size_t)tile * kRadix, kFlagAgg | tcount);
             excl = lookback_walk(st, kRadix, (int64_t)tile - 1, wc);
-            if (publish) st_release(st + (size_t)tile * kRadix, kFlagInc | ((excl + tcount) & kValMask));
+            if (publish) st_publish(st + (size_t)tile * kRadix, kFlagInc | ((excl + tcount) & kValMask));
         }
         S.gbase[d] = digit_off[d] + excl;
     }

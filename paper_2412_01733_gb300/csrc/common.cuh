@@ -200,8 +200,11 @@ struct TreeWorkspace {
 namespace treegb {
 
 // ---------------------------------------------------------------- device helpers
-__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+// Look-back words are published with relaxed stores at GPU scope: a reader
+// reads nothing but the word itself (flag and value share it), so no earlier
+// write has to become visible with it, and a release fence would only stall.
+__device__ __forceinline__ void st_publish(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -321,12 +324,12 @@ __device__ inline uint32_t lookback_walk(const uint32_t *st, size_t stride, int6
 // the limit gives up as in lookback_walk (every waiter terminates).
 __device__ inline uint32_t lookback_single(uint32_t *status, uint32_t tile, uint32_t agg, const WaitCtx &wc) {
     if (tile == 0) {
-        st_release(status, kFlagInc | (agg & kValMask));
+        st_publish(status, kFlagInc | (agg & kValMask));
         return 0;
     }
-    st_release(status + tile, kFlagAgg | (agg & kValMask));
+    st_publish(status + tile, kFlagAgg | (agg & kValMask));
     const uint32_t excl = lookback_walk(status, 1, (int64_t)tile - 1, wc);
-    st_release(status + tile, kFlagInc | ((excl + agg) & kValMask));
+    st_publish(status + tile, kFlagInc | ((excl + agg) & kValMask));
     return excl;
 }
 
