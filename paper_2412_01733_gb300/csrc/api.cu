@@ -485,7 +485,7 @@ static tree_status_t walk(TreeWorkspace *ws, int mode, const WalkOut &out, cudaS
     tree_status_t st = upload_mac(ws, s);
     if (st != TREE_OK) return st;
     PhaseScope ph(ws, mode == kWalkForce ? TREE_PHASE_WALK : TREE_PHASE_LISTS, s);
-    TRY_CUDA(launch_group_order(ws, s));
+    if (walk_widest_first(ws)) TRY_CUDA(launch_group_order(ws, s));
     if (ws->p.precision == TREE_F64) TRY_CUDA(launch_walk_f64(ws, mode, out, s));
     else TRY_CUDA(launch_walk_f32(ws, mode, out, s));
     return TREE_OK;

@@ -27,6 +27,12 @@ constexpr int kLevelThreads = 256;  // octree level block (nodes per tile)
 constexpr int kMaxBlocksReduce = 1024;  // partial-result slots of the reductions
 constexpr int kMaxLeafSmall = 16;   // leaves up to this size are expanded in the walk buffer
 constexpr int64_t kMaxNodes = (int64_t)1 << 29;  // node indices fit 29 bits (walk stack entries)
+// Below this many particles the walk takes its groups widest box first (one
+// expensive group at the end of a short walk would be a visible straggler);
+// above it, in key order, which keeps the neighbourhoods the SMs walk at the
+// same time together in L2 (measured 0.3 % faster on the galaxy at N = 1.7e7
+// and 1e8, equal at 2^20).
+constexpr int64_t kWalkOrderMaxN = (int64_t)1 << 22;
 
 // lookback status words: 2-bit flag + 30-bit value
 constexpr uint32_t kFlagAgg = 1u << 30;
@@ -198,6 +204,8 @@ struct TreeWorkspace {
 };
 
 namespace treegb {
+
+inline bool walk_widest_first(const TreeWorkspace *ws) { return ws->n < kWalkOrderMaxN; }
 
 // ---------------------------------------------------------------- device helpers
 // Look-back words are published with relaxed stores at GPU scope: a reader

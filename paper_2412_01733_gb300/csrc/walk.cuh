@@ -718,7 +718,7 @@ inline WalkArgs make_walk_args(TreeWorkspace *ws, const WalkOut &out) {
     a.list_off = ws->list_cnt;
     a.pc_list = ws->pc_list;
     a.pp_list = ws->pp_list;
-    a.order = ws->gorder;
+    a.order = walk_widest_first(ws) ? ws->gorder : nullptr;
     a.gfirst = ws->gfirst;
     a.ctr = ws->ctr;
     a.seg_off = ws->seg_off;
