@@ -24,7 +24,7 @@ def tg():
 def _declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b((?:tree|leapfrog)_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b((?:tree|leapfrog)_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_symbols_exported(tg):
