@@ -639,7 +639,8 @@ def study_theta(a):
 def study_threads(a):
     """The paper's own measurement (Sec. 3, Eqs. 6-7) on the FP64 CPU oracle: mean time T(M) of one tree
     force evaluation over 10 repetitions with its standard error, speedup S = T(1)/T(M) and efficiency
-    E = S/M, for M host threads, galaxy recipe at N = 1e5 and 1e6, theta = 1."""
+    E = S/M, for M host threads, galaxy recipe at N = 1e5, 1e6 and 1e7, theta = 1, and E against N at M = 4
+    for N = 2^17 .. 2^24."""
     import os as _os
 
     import numpy as np
@@ -649,20 +650,21 @@ def study_threads(a):
     from paper_2412_01733_gb300 import inputs
     ncpu = _os.cpu_count() or 1
     ms_list = sorted({1, 2, 4, 8, ncpu // 2, ncpu} - {0})
-    for n in (100_000, 1_000_000):
+    for n in (100_000, 1_000_000, 10_000_000):
         x, _, m = inputs.galaxy(n, SEED, dtype=torch.float64)
         x, m = x.numpy(), m.numpy()
         res = {}
-        for M in ms_list:
+        # N = 1e7: one evaluation per thread count (about 200 s on one Grace core), at 1, 4 and all threads
+        for M in (ms_list if n <= 1_000_000 else sorted({1, 4, ncpu})):
             O.set_threads(M)
-            reps = 10 if n <= 100_000 else 5
+            reps = 10 if n <= 100_000 else (5 if n <= 1_000_000 else 1)
             ts = []
             for _ in range(reps):
                 t0 = time.perf_counter()
                 O.tree_forces(x, m, eps=PARAMS["eps"], theta=1.0, lcap=PARAMS["leaf_cap"], gs=PARAMS["group_size"])
                 ts.append(time.perf_counter() - t0)
             ts = np.array(ts)
-            res[M] = (ts.mean(), ts.std(ddof=1) / np.sqrt(len(ts)))
+            res[M] = (ts.mean(), ts.std(ddof=1) / np.sqrt(len(ts)) if len(ts) > 1 else 0.0)
         T1, dT1 = res[1]
         for M, (T, dT) in res.items():
             S = T1 / T
@@ -679,8 +681,9 @@ def study_threads(a):
         O.direct(x, m, eps=PARAMS["eps"])
         print(json.dumps({"study": "threads_direct", "n": 1 << 15, "threads": M, "T_s": time.perf_counter() - t0}),
               flush=True)
-    # efficiency against N at M = 4 threads (the paper's E(N) view), N = 2^17 .. 2^21
-    for lg in range(17, 22):
+    # efficiency against N at M = 4 threads (the paper's E(N) view), N = 2^17 .. 2^24 (one evaluation
+    # per thread count above 2^21)
+    for lg in range(17, 25):
         n = 1 << lg
         x, _, m = inputs.galaxy(n, SEED, dtype=torch.float64)
         x, m = x.numpy(), m.numpy()
@@ -688,7 +691,7 @@ def study_threads(a):
         for M in (1, 4):
             O.set_threads(M)
             ts = []
-            for _ in range(2):
+            for _ in range(2 if lg <= 21 else 1):
                 t0 = time.perf_counter()
                 O.tree_forces(x, m, eps=PARAMS["eps"], theta=1.0, lcap=PARAMS["leaf_cap"], gs=PARAMS["group_size"])
                 ts.append(time.perf_counter() - t0)

@@ -394,3 +394,41 @@ def test_export_lists_groups_matches_full_export():
     with pytest.raises(tg.TreeError) as e:
         ws.export_lists_groups([ng])
     assert e.value.code == tg.TREE_ERR_ARG
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_host_state_step_equals_device_step(precision):
+    """leapfrog_step_host (state in pinned host memory, copies inside the call,
+    x copied back under the walk) gives exactly the device-resident step: the
+    same kernels on the same data."""
+    tg = _tg()
+    n, tau = 20011, 0.005
+    x, v, m = inputs.galaxy(n, 5)
+    dt = torch.float64 if precision == "f64" else torch.float32
+    xg, vg, mg = (t.to("cuda", dt).contiguous() for t in (x, v, m))
+    p = dict(eps=0.02, theta=0.6, order=2, leaf_cap=16, group_size=32, precision=precision)
+    with tg.Workspace(n, **p) as wd, tg.Workspace(n, **p) as wh:
+        a, phi = wd.accel(xg, mg)
+        xh, vh, mh, ah = (t.cpu().pin_memory() for t in (xg, vg, mg, a))
+        ph = torch.empty(n, dtype=dt).pin_memory()
+        dh = torch.empty(8, dtype=torch.float64).pin_memory()
+        diag = torch.empty(8, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            wd.leapfrog_step(xg, vg, mg, a, tau, phi=phi)
+            wd.diagnostics(xg, vg, mg, phi, out=diag)
+            wh.leapfrog_step_host(xh, vh, mh, ah, tau, phi=ph, diag=dh)
+        torch.cuda.synchronize()
+        assert wd.status() == 0 and wh.status() == 0
+        for dev_t, host_t in ((xg, xh), (vg, vh), (a, ah), (phi, ph), (diag, dh)):
+            assert torch.equal(dev_t.cpu(), host_t)
+
+
+def test_fp32_peak_probe():
+    """The FP32 FMA peak the roofline is reported against: positive, below the
+    unit-count bound (152 SMs x 128 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s,
+    with a small margin for clock reporting), packed at least as fast as scalar
+    within a few percent."""
+    tg = _tg()
+    scalar, packed = tg.fp32_peak()
+    assert 10.0 < scalar < 82.0 and 10.0 < packed < 82.0, (scalar, packed)
+    assert packed > 0.9 * scalar
