@@ -271,12 +271,13 @@ def run_ours(a):
 
     if not a.no_extras:
         # end to end through the C ABI with host-resident state (first among the extras, right after
-        # the timed steps): leapfrog_step_host copies x, v, m, a up, runs the step and the diagnostics,
-        # and copies x (under the tree build and walk), v, a, phi and the diagnostics back
+        # the timed steps): leapfrog_step_host copies the state x, v, m, a up, runs the step and the
+        # diagnostics, and copies the new state x (under the tree build and walk), v, a and the
+        # diagnostics (which carry W) back
         xh = x.cpu().pin_memory(); vh = v.cpu().pin_memory(); mh = m.cpu().pin_memory()
-        ah = acc.cpu().pin_memory(); ph = phi.cpu().pin_memory()
+        ah = acc.cpu().pin_memory()
         dh = torch.empty(8, dtype=torch.float64).pin_memory()
-        ws.leapfrog_step_host(xh, vh, mh, ah, TAU, phi=ph, diag=dh)
+        ws.leapfrog_step_host(xh, vh, mh, ah, TAU, diag=dh)
         torch.cuda.synchronize()
         barrier()
         clocks_e2e = Clocks(local)
@@ -285,7 +286,7 @@ def run_ours(a):
         h0 = torch.cuda.Event(enable_timing=True); h1 = torch.cuda.Event(enable_timing=True)
         h0.record(stream)
         for _ in range(a.steps):
-            ws.leapfrog_step_host(xh, vh, mh, ah, TAU, phi=ph, diag=dh)
+            ws.leapfrog_step_host(xh, vh, mh, ah, TAU, diag=dh)
         h1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -298,14 +299,14 @@ def run_ours(a):
         split = {"h2d_ms": ph_e2e["h2d"][0] / a.steps, "d2h_after_walk_ms": ph_e2e["d2h"][0] / a.steps,
                  "walk_ms": ph_e2e["walk"][0] / a.steps, "step_ms": te * 1e3 / a.steps}
         out["e2e"] = {"value": world * n * a.steps / te, "unit": UNIT,
-                      "h2d_bytes_per_step": 40 * n, "d2h_bytes_per_step": 40 * n + 64, "clocks": ck_e2e,
+                      "h2d_bytes_per_step": 40 * n, "d2h_bytes_per_step": 36 * n + 64, "clocks": ck_e2e,
                       "api": "leapfrog_step_host (pinned host arrays; x copied back on a second stream under "
                              "the tree build and walk)",
                       "per_step": {k: round(v, 2) for k, v in split.items()}}
-        # continue from the host state: device arrays take it back
-        x.copy_(xh); v.copy_(vh); acc.copy_(ah); phi.copy_(ph)
+        # continue from the host state: the device arrays take it back
+        x.copy_(xh); v.copy_(vh); acc.copy_(ah)
         torch.cuda.synchronize()
-        del xh, vh, mh, ah, ph, dh
+        del xh, vh, mh, ah, dh
         # force error of the FP32 tree against the GPU FP64 direct sum of Eq. 1 (sampled particles;
         # the state after the end-to-end steps, whose accelerations belong to these positions)
         out["force_err_vs_direct"] = force_error(ws, x, m, acc, comp, a.err_samples, a.err_samples_fp64)
