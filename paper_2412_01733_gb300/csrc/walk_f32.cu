@@ -1,5 +1,7 @@
 // walk_f32.cu -- FP32 tree walk: FP32 positions, moments and pair terms,
 // optional Kahan-compensated per-particle sums.
+#include <cfloat>
+
 #include "walk.cuh"
 
 namespace treegb {
@@ -28,7 +30,11 @@ cudaError_t launch_walk_f32(TreeWorkspace *ws, int mode, const WalkOut &out, cud
     if (mode == kWalkEmit)
         return two ? walk_run<float, 2, false, false, true, kWalkEmit>(ws, a, s)
                    : walk_run<float, 1, false, false, true, kWalkEmit>(ws, a, s);
-    const bool quad = ws->p.order == 2, kahan = ws->p.kahan != 0, soft = ws->p.eps > 0.0;
+    // the softened pair terms need eps^2 to be a normal FP32 number (see
+    // rsqrt_pair); a smaller eps^2 takes the unsoftened variant, which still
+    // adds it to r^2 and drops coincident pairs
+    const bool quad = ws->p.order == 2, kahan = ws->p.kahan != 0;
+    const bool soft = (float)(ws->p.eps * ws->p.eps) >= FLT_MIN;
     return two ? dispatch_f32<2>(ws, a, quad, kahan, soft, s) : dispatch_f32<1>(ws, a, quad, kahan, soft, s);
 }
 
