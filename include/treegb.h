@@ -96,7 +96,10 @@ typedef struct {
     int32_t leaf_cap;    /* maximum particles of an internal-free cell, 1..16 (paper: 1) */
     int32_t group_size;  /* particles per walk group: 16, 32 or 64 */
     int32_t stack_depth; /* walk stack entries per warp, 256..8192, a multiple of 32 */
-    int32_t precision;   /* TREE_F32 or TREE_F64 */
+    int32_t precision;   /* TREE_F32 or TREE_F64.  TREE_F32 forms r^-5 for the quadrupole
+                            terms: distances up to 2^25 (3.4e7) in the units of x keep it a
+                            normal FP32 number; beyond, the quadrupole correction loses
+                            precision gradually (the monopole term does not) */
     int32_t kahan;       /* FP32: 1 = compensated per-particle accumulation */
     int32_t group_split; /* delta: cut a group between neighbours that do not share the cell
                             delta levels above the finer of their leaves, or whose smallest

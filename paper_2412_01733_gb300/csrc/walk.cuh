@@ -54,6 +54,7 @@ struct WalkArgs {
     uint32_t *ctr;            // counter block: group count and the walk's group ticket
     const int64_t *seg_off;   // segment offsets (nseg > 1): a group walks its own segment's tree
     int64_t nseg;
+    const DevBox *box;        // per segment: the tree's cube (side 2^k)
 };
 
 template <typename Real> __device__ __forceinline__ Real rsqrt_r(Real x);
@@ -169,10 +170,26 @@ __device__ __forceinline__ void pp_pair(float2 nx, float2 ny, float2 nz, float2 
     acc[3] = __ffma2_rn(neg1, mr, acc[3]);
 }
 
+// Whether the R5 form of pc_pair stays in the normal FP32 range for every
+// far cell of a segment whose tree is the cube of side L = 2^k and whose total
+// mass is M_root: a cell and a target lie in that cube, so r <= sqrt(3) L and
+// |M r^2 u| <= M_root (sqrt(3) L)^3.  k <= 24 keeps r^-5 >= 4.8e-38 (FLT_MIN =
+// 1.2e-38) and the mass bound keeps M r^2 u <= 1e37.  (At small r both forms
+// form r^-5 alike.)
+__device__ __forceinline__ bool pc_r5_fits(int k, float m_root) {
+    if (k > 24) return false;
+    const float span = 1.7320508f * ldexpf(1.0f, max(k, -40));
+    return m_root * span * span * span <= 1e37f;
+}
+
 // PC for two cells.  With u = R - r_i (= -y) and the negated quadrupole
 // Qn = -Q (the FP32 cell copies store -Q), w = Qn u equals Q y, u.w = -(y.Q.y), and the terms of
 // pc_term become a = [M/r^3 - 5/2 (u.w)/r^7] u + w/r^5, phi = -M/r + 1/2 (u.w)/r^5.
-template <bool QUAD, bool SOFT>
+// R5 (quadrupole only) takes r^-5 out of the acceleration, a = r^-5 (k u + w) with
+// k = M r^2 - 5/2 (u.w)/r^2, and accumulates -phi = [M - 1/2 (u.w)/r^4] / r in acc[3]
+// (neg1 must then hold -1/2): 33 packed operations for two cells instead of 34.  It forms
+// r^-5 and M r^2 u, so the walk takes it only where pc_r5_fits holds.
+template <bool QUAD, bool SOFT, bool R5 = false>
 __device__ __forceinline__ void pc_pair(float2 nx, float2 ny, float2 nz, const float4 &A, const float4 &B,
                                         const float4 &C, const float4 &D, const float4 &E, float2 eps2,
                                         float2 neg1, float2 half, float2 m25, float2 (&acc)[4]) {
@@ -193,14 +210,24 @@ __device__ __forceinline__ void pc_pair(float2 nx, float2 ny, float2 nz, const f
         const float2 wy = __ffma2_rn(qxy, ux, __ffma2_rn(qyy, uy, __fmul2_rn(qyz, uz)));
         const float2 wz = __ffma2_rn(qxz, ux, __ffma2_rn(qyz, uy, __fmul2_rn(qzz, uz)));
         const float2 uw = __ffma2_rn(ux, wx, __ffma2_rn(uy, wy, __fmul2_rn(uz, wz)));
-        const float2 r3 = __fmul2_rn(ri, ri2);
-        const float2 r5 = __fmul2_rn(r3, ri2);
-        const float2 t = __fmul2_rn(uw, r5);
-        const float2 c = __ffma2_rn(t, __fmul2_rn(ri2, m25), Mr3);
-        acc[0] = __ffma2_rn(c, ux, __ffma2_rn(r5, wx, acc[0]));
-        acc[1] = __ffma2_rn(c, uy, __ffma2_rn(r5, wy, acc[1]));
-        acc[2] = __ffma2_rn(c, uz, __ffma2_rn(r5, wz, acc[2]));
-        acc[3] = __ffma2_rn(neg1, Mr, __ffma2_rn(half, t, acc[3]));
+        if (R5) {
+            const float2 ri4 = __fmul2_rn(ri2, ri2);
+            const float2 r5 = __fmul2_rn(ri4, ri);
+            const float2 k = __ffma2_rn(m25, __fmul2_rn(uw, ri2), __fmul2_rn(M, r2));
+            acc[0] = __ffma2_rn(r5, __ffma2_rn(k, ux, wx), acc[0]);
+            acc[1] = __ffma2_rn(r5, __ffma2_rn(k, uy, wy), acc[1]);
+            acc[2] = __ffma2_rn(r5, __ffma2_rn(k, uz, wz), acc[2]);
+            acc[3] = __ffma2_rn(ri, __ffma2_rn(uw, __fmul2_rn(ri4, neg1), M), acc[3]);
+        } else {
+            const float2 r3 = __fmul2_rn(ri, ri2);
+            const float2 r5 = __fmul2_rn(r3, ri2);
+            const float2 t = __fmul2_rn(uw, r5);
+            const float2 c = __ffma2_rn(t, __fmul2_rn(ri2, m25), Mr3);
+            acc[0] = __ffma2_rn(c, ux, __ffma2_rn(r5, wx, acc[0]));
+            acc[1] = __ffma2_rn(c, uy, __ffma2_rn(r5, wy, acc[1]));
+            acc[2] = __ffma2_rn(c, uz, __ffma2_rn(r5, wz, acc[2]));
+            acc[3] = __ffma2_rn(neg1, Mr, __ffma2_rn(half, t, acc[3]));
+        }
     } else {
         acc[0] = __ffma2_rn(Mr3, ux, acc[0]);
         acc[1] = __ffma2_rn(Mr3, uy, acc[1]);
@@ -234,7 +261,7 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 }
 
 template <typename Real, int TPL, bool QUAD, bool KAHAN, bool SOFT, int MODE>
-__global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(const WalkArgs A) {
+__global__ void __launch_bounds__(kWalkWarps * 32, TPL == 2 ? 4 : sizeof(Real) == 4 ? 6 : 5) k_walk(const WalkArgs A) {
     using V4 = typename Vec4<Real>::T;
     using V2 = typename Vec2<Real>::T;
     extern __shared__ __align__(32) unsigned char smem[];
@@ -262,6 +289,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
     const V2 *__restrict__ momC = reinterpret_cast<const V2 *>(A.mom_c);
     const Real eps2 = (Real)A.eps2;
 
+    // full far-cell tiles of one-target-per-lane groups take pc_pair's R5 form
+    // where it fits the segment's cube (one tree: decided once per block)
+    constexpr bool kR5 = sizeof(Real) == 4 && QUAD && TPL == 1;
+    const bool r5_tree = kR5 && A.nseg == 1 && pc_r5_fits(A.box[0].k, (float)momA[0].w);
+
     // persistent warps: each takes the next group slot until all are done
     const uint32_t ngroups = A.ctr[kCtrGroups];
     for (;;) {
@@ -272,6 +304,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
     const int64_t g = A.order ? (int64_t)A.order[slot] : (int64_t)slot;
     const int64_t s0 = A.gfirst[g];
     const int cnt = (int)(A.gfirst[g + 1] - A.gfirst[g]);
+    // the group's segment b (its tree's root is node b)
+    const uint32_t gseg = A.nseg > 1 ? seg_find(A.seg_off, A.nseg, s0) : 0u;
 
     // targets and the group's integer box
     Real px[TPL], py[TPL], pz[TPL], pm[TPL];
@@ -313,7 +347,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
         nZ[t] = make_float2(-(float)pz[t], -(float)pz[t]);
     }
     const float2 eps2v = make_float2((float)A.eps2, (float)A.eps2);
-    const float2 neg1 = make_float2(-1.f, -1.f), halfv = make_float2(0.5f, 0.5f), m25 = make_float2(-2.5f, -2.5f);
+    const float2 neg1 = make_float2(-1.f, -1.f), halfv = make_float2(0.5f, 0.5f), m25 = make_float2(-2.5f, -2.5f),
+                 mhalf = make_float2(-0.5f, -0.5f);
+    bool r5 = r5_tree;
+    if (kR5 && A.nseg > 1) r5 = pc_r5_fits(A.box[gseg].k, (float)momA[gseg].w);
 
     // true when some staged source is one of the group's own particles
     auto stage_pp = [&](const V4 &src, uint32_t si, int ns) -> bool {
@@ -448,7 +485,18 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
                 for (int c = 0; c < 4; ++c) part[t][c] = make_float2(0.f, 0.f);
             const int np = (ns + 1) >> 1;
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (np == 16) {
+            const bool tile_r5 = np == 16 && r5;  // part[t][3] then holds -phi
+            if (tile_r5) {
+#pragma unroll 16
+                for (int k = 0; k < 16; ++k) {
+                    const float4 a = stF[5 * k], b = stF[5 * k + 1];
+                    const float4 c = stF[5 * k + 2], d = stF[5 * k + 3], e = stF[5 * k + 4];
+#pragma unroll
+                    for (int t = 0; t < TPL; ++t)
+                        pc_pair<QUAD, SOFT, true>(nX[t], nY[t], nZ[t], a, b, c, d, e, eps2v, mhalf, halfv, m25,
+                                                  part[t]);
+                }
+            } else if (np == 16) {
 #pragma unroll 4
                 for (int k = 0; k < 16; ++k) {
                     const float4 a = stF[5 * k], b = stF[5 * k + 1];
@@ -473,6 +521,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
                 Real p1[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) p1[c] = (Real)(part[t][c].x + part[t][c].y);
+                if (tile_r5) p1[3] = -p1[3];
                 fold<Real, KAHAN>(sum[t], cmp[t], p1);
             }
             __syncwarp();
@@ -513,7 +562,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 4) k_walk(cons
     int top = 1, npc = 0, npp = 0;
     // Stack entries are child ranges: first node | (count - 1) << 29.
     // the root of the group's segment (node b at level 0): range (node b, 1 node)
-    if (lane == 0) stack[0] = A.nseg > 1 ? seg_find(A.seg_off, A.nseg, s0) : 0u;
+    if (lane == 0) stack[0] = gseg;
     __syncwarp();
     bool overflow = false;
     while (top > 0) {
@@ -737,6 +786,7 @@ inline WalkArgs make_walk_args(TreeWorkspace *ws, const WalkOut &out) {
     a.ctr = ws->ctr;
     a.seg_off = ws->seg_off;
     a.nseg = ws->nseg;
+    a.box = ws->box;
     return a;
 }
 

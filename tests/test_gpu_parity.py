@@ -168,6 +168,33 @@ def test_kahan_off_still_within_tolerance(orc):
     assert np.median(e) <= 1e-5
 
 
+def test_far_cell_forms_agree(orc):
+    """The FP32 walk evaluates full far-cell tiles with the quadrupole term's
+    r^-5 taken out of the acceleration when the tree's cube is at most 2^24 on a
+    side, and with the full form otherwise.  Scaling positions and eps by a power
+    of two leaves the tree unchanged and scales every FP32 operation exactly; the
+    scale here puts the cube at 2^25, past that limit but with r^-5 still within
+    a few binades of the normal range (>= 20 bits).  a * s^2 and phi * s of the
+    scaled run (full form) must match the unscaled run (r^-5 form) to FP32
+    rounding, and the scaled run must match the oracle."""
+    x, m = _gen("galaxy", 40000)
+    p = dict(theta=0.7, order=2, leaf_cap=16, group_size=32)
+    ws1, xg1, mg1, a1, phi1 = _run(x, m, emit=False, eps=0.02, **p)
+    k = ws1.info()["box_k"]
+    assert k <= 24
+    s = 2.0 ** (25 - k)
+    ws2, xg2, mg2, a2, phi2 = _run(x * s, m, emit=False, eps=0.02 * s, **p)
+    assert ws1.status() == 0 and ws2.status() == 0 and ws2.info()["box_k"] == 25
+    np.testing.assert_array_equal(ws1.export_tree()["perm"].cpu().numpy(), ws2.export_tree()["perm"].cpu().numpy())
+    e = _rel_err(_np64(a2) * s * s, _np64(a1))
+    assert np.median(e) <= 1e-6 and e.max() <= 1e-4, (np.median(e), e.max())
+    ep = np.abs(_np64(phi2) * s - _np64(phi1)) / np.abs(_np64(phi1))
+    assert np.median(ep) <= 1e-6 and ep.max() <= 1e-4, (np.median(ep), ep.max())
+    ref = orc.tree_forces(_np64(xg2), _np64(mg2), eps=0.02 * s, theta=0.7, lcap=16, gs=32, quad=True)
+    e2 = _rel_err(_np64(a2), ref.a)
+    assert np.median(e2) <= 1e-5 and e2.max() <= 1e-4, (np.median(e2), e2.max())
+
+
 def test_theta_zero_equals_direct_sum(orc):
     x, m = _gen("plummer", 4000)
     ws, xg, mg, a, phi = _run(x, m, eps=0.01, theta=0.0, order=2, leaf_cap=16, group_size=32)
