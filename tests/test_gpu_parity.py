@@ -195,6 +195,35 @@ def test_far_cell_forms_agree(orc):
     assert np.median(e2) <= 1e-5 and e2.max() <= 1e-4, (np.median(e2), e2.max())
 
 
+def test_keys_exact_near_cell_boundaries(orc):
+    """FP32 coordinates are quantised in FP32 arithmetic where that provably
+    gives the FP64 definition's cell and in FP64 otherwise.  Points on cell
+    boundaries, one or two ulps either side of them, tiny coordinates 2^-60 or
+    more below the box corner's magnitude (where the FP64 subtraction rounds)
+    and zeros must get the oracle's keys bit for bit."""
+    rng = np.random.default_rng(5)
+    k, lo = 4, -8.0
+    unit = 2.0 ** (k - 21)
+    g = (lo + rng.integers(0, 2 ** 21, size=(3, 4000)) * unit).astype(np.float32)
+    up, down = np.nextafter(g, np.float32(np.inf)), np.nextafter(g, np.float32(-np.inf))
+    up2 = np.nextafter(up, np.float32(np.inf))
+    tiny = (rng.uniform(-1.0, 1.0, size=(3, 2000)) * 10.0 ** rng.integers(-30, -18, size=(3, 2000))).astype(np.float32)
+    x = np.concatenate([np.full((3, 1), lo, np.float32), g, up, down, up2, tiny, np.zeros((3, 50), np.float32)], axis=1)
+    x = np.clip(x, np.float32(lo), np.float32(7.5))
+    m = np.full(x.shape[1], 1.0 / x.shape[1])
+    ws, xg, mg, a, phi = _run(torch.from_numpy(x.astype(np.float64)), torch.from_numpy(m), emit=False, eps=0.01,
+                              theta=0.7, order=2, leaf_cap=16, group_size=32)
+    assert ws.status() == 0 and ws.info()["box_k"] == k
+    x64 = _np64(xg)
+    blo, bk = orc.box(x64)
+    assert bk == k and np.all(blo == lo)
+    _, key = orc.keys(x64, blo, bk)
+    perm = orc.sort(key)
+    ex = ws.export_tree()
+    np.testing.assert_array_equal(ex["keys"].cpu().numpy().astype(np.uint64), key[perm])
+    np.testing.assert_array_equal(ex["perm"].cpu().numpy().astype(np.int64), perm)
+
+
 def test_theta_zero_equals_direct_sum(orc):
     x, m = _gen("plummer", 4000)
     ws, xg, mg, a, phi = _run(x, m, eps=0.01, theta=0.0, order=2, leaf_cap=16, group_size=32)
