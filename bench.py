@@ -50,7 +50,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM bytes per walk launch from ncu (dram__bytes_read.sum + write.sum) on the
 # N = 1e7 galaxy case of the same kernel, per particle (scaled by N below);
 # None when the kernel has changed since the counters were taken.
-WALK_DRAM_BYTES_PER_PARTICLE = 713
+WALK_DRAM_BYTES_PER_PARTICLE = 716
 WALK_TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_walk, galaxy N=1e7, scaled by N"
 
 

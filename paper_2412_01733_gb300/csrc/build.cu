@@ -70,6 +70,7 @@ __device__ void box_from_minmax(double (&lo)[3], double (&hi)[3], DevBox *box) {
     if (ext > 0.0) frexp(ext, &k);
     for (int d = 0; d < 3; ++d) box->lo[d] = lo[d];
     box->k = k;
+    box->r5fit = 0;  // decided after the moments
     box->scale = ldexp(1.0, kBits - k);
     box->unit = ldexp(1.0, k - kBits);
 }

@@ -57,7 +57,7 @@ struct DevBox {
     double scale;   // 2^(21-k)
     double unit;    // 2^(k-21): grid spacing
     int32_t k;
-    int32_t pad;
+    int32_t r5fit;  // set after the moments: the FP32 walk's r^-5 far-cell form fits (pc_r5_fits)
 };
 
 // Offsets into the counter block (uint32), cleared at the start of a build.
@@ -279,6 +279,19 @@ struct WaitCtx {
 
 // True when a bounded wait of an earlier stage of this build gave up: the
 // calling kernel (of stage `stage`) must return without touching the data.
+// Whether the FP32 walk's quadrupole far-cell term with r^-5 taken out of the
+// acceleration (pc_pair's R5 form) stays in the normal FP32 range for every
+// far cell of a segment whose tree is the cube of side L = 2^k and whose total
+// mass is M_root: a cell and a target lie in that cube, so r <= sqrt(3) L and
+// |M r^2 u| <= M_root (sqrt(3) L)^3.  k <= 24 keeps r^-5 >= 4.8e-38 (FLT_MIN =
+// 1.2e-38) and the mass bound keeps M r^2 u <= 1e37.  (At small r the full
+// form forms r^-5 as well.)
+__device__ __forceinline__ bool pc_r5_fits(int k, float m_root) {
+    if (k > 24) return false;
+    const float span = 1.7320508f * ldexpf(1.0f, max(k, -40));
+    return m_root * span * span * span <= 1e37f;
+}
+
 __device__ __forceinline__ bool aborted(const uint32_t *ctr, uint32_t stage) {
     const uint32_t a = ctr[kCtrAbort];
     return a != 0u && a != stage;

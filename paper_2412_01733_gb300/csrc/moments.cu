@@ -206,6 +206,15 @@ __global__ void __launch_bounds__(256) k_moments_level(
     }
 }
 
+// Per segment b (its root is node b), whether the FP32 walk may take its
+// r^-5 far-cell form: pc_r5_fits of the segment's cube and root mass.
+__global__ void __launch_bounds__(256) k_r5_flags(const uint32_t *__restrict__ ctr, DevBox *box,
+                                                  const float4 *__restrict__ mom_a, int64_t nseg) {
+    if (aborted(ctr, kStageAfter)) return;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nseg; b += (int64_t)gridDim.x * blockDim.x)
+        box[b].r5fit = pc_r5_fits(box[b].k, mom_a[b].w) ? 1 : 0;
+}
+
 template <typename Real>
 static cudaError_t moments_impl(TreeWorkspace *ws, cudaStream_t s) {
     using V4 = typename Vec4<Real>::T;
@@ -226,6 +235,11 @@ static cudaError_t moments_impl(TreeWorkspace *ws, cudaStream_t s) {
                                                  ws->seg_off, ws->nseg, ws->mom64, ws->node_cap, (V4 *)ws->mom_a,
                                                  (V4 *)ws->mom_b, (V2 *)ws->mom_c);
     ws->launches += 3 + kMaxLevel;
+    if (sizeof(Real) == 4) {
+        k_r5_flags<<<grid_for(ws->nseg, 256, 152), 256, 0, s>>>(ws->ctr, ws->box, (const float4 *)ws->mom_a,
+                                                               ws->nseg);
+        ws->launches += 1;
+    }
     return cudaGetLastError();
 }
 

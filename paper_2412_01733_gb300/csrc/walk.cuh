@@ -170,18 +170,6 @@ __device__ __forceinline__ void pp_pair(float2 nx, float2 ny, float2 nz, float2 
     acc[3] = __ffma2_rn(neg1, mr, acc[3]);
 }
 
-// Whether the R5 form of pc_pair stays in the normal FP32 range for every
-// far cell of a segment whose tree is the cube of side L = 2^k and whose total
-// mass is M_root: a cell and a target lie in that cube, so r <= sqrt(3) L and
-// |M r^2 u| <= M_root (sqrt(3) L)^3.  k <= 24 keeps r^-5 >= 4.8e-38 (FLT_MIN =
-// 1.2e-38) and the mass bound keeps M r^2 u <= 1e37.  (At small r both forms
-// form r^-5 alike.)
-__device__ __forceinline__ bool pc_r5_fits(int k, float m_root) {
-    if (k > 24) return false;
-    const float span = 1.7320508f * ldexpf(1.0f, max(k, -40));
-    return m_root * span * span * span <= 1e37f;
-}
-
 // PC for two cells.  With u = R - r_i (= -y) and the negated quadrupole
 // Qn = -Q (the FP32 cell copies store -Q), w = Qn u equals Q y, u.w = -(y.Q.y), and the terms of
 // pc_term become a = [M/r^3 - 5/2 (u.w)/r^7] u + w/r^5, phi = -M/r + 1/2 (u.w)/r^5.
@@ -290,9 +278,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 2 ? 4 : sizeof(Real) =
     const Real eps2 = (Real)A.eps2;
 
     // full far-cell tiles of one-target-per-lane groups take pc_pair's R5 form
-    // where it fits the segment's cube (one tree: decided once per block)
+    // where it fits the segment's cube (flag set per segment after the moments)
     constexpr bool kR5 = sizeof(Real) == 4 && QUAD && TPL == 1;
-    const bool r5_tree = kR5 && A.nseg == 1 && pc_r5_fits(A.box[0].k, (float)momA[0].w);
 
     // persistent warps: each takes the next group slot until all are done
     const uint32_t ngroups = A.ctr[kCtrGroups];
@@ -349,8 +336,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 2 ? 4 : sizeof(Real) =
     const float2 eps2v = make_float2((float)A.eps2, (float)A.eps2);
     const float2 neg1 = make_float2(-1.f, -1.f), halfv = make_float2(0.5f, 0.5f), m25 = make_float2(-2.5f, -2.5f),
                  mhalf = make_float2(-0.5f, -0.5f);
-    bool r5 = r5_tree;
-    if (kR5 && A.nseg > 1) r5 = pc_r5_fits(A.box[gseg].k, (float)momA[gseg].w);
+    const bool r5 = kR5 && A.box[gseg].r5fit != 0;
 
     // true when some staged source is one of the group's own particles
     auto stage_pp = [&](const V4 &src, uint32_t si, int ns) -> bool {
