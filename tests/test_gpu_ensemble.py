@@ -120,6 +120,28 @@ def test_ensemble_equals_each_system_alone(orc):
         assert np.median(ep) <= 1e-5 and ep.max() <= 1e-4
 
 
+def test_ensemble_mixed_far_cell_forms():
+    """The FP32 walk chooses its far-cell form per segment (the r^-5 form only
+    where the segment's cube is at most 2^24 on a side): an ensemble holding a
+    system with a small cube and the same system scaled past 2^24 gives each
+    system the forces it gets alone, bit for bit."""
+    tg = _tg()
+    x, _, m = inputs.galaxy(3000, 21)
+    w1 = tg.Workspace(3000, **P)
+    w1.build(x.float().cuda().contiguous())
+    s = 2.0 ** (25 - w1.info()["box_k"])
+    x2 = torch.cat([x, x * s], 1)
+    m2 = torch.cat([m, m])
+    off = np.array([0, 3000, 6000], np.int64)
+    xe, me = x2.float().cuda().contiguous(), m2.float().cuda().contiguous()
+    ws, a, phi = _run(tg, xe, me, off, **P)
+    _, kb = ws.export_boxes()
+    assert int(kb[0]) <= 24 and int(kb[1]) == 25
+    for b0, b1 in ((0, 3000), (3000, 6000)):
+        wa, aa, pa = _run(tg, xe[:, b0:b1].contiguous(), me[b0:b1].contiguous(), **P)
+        assert torch.equal(a[:, b0:b1], aa) and torch.equal(phi[b0:b1], pa)
+
+
 def test_ensemble_leapfrog_and_diagnostics_equal_alone():
     tg = _tg()
     x, v, m, off = _mixed_ensemble(seed=23)
