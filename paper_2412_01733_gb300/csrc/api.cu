@@ -88,6 +88,11 @@ void free_all(TreeWorkspace *ws) {
     if (ws->ev_xback) cudaEventDestroy(ws->ev_xback);
     ws->copy_stream = nullptr;
     ws->ev_drift = ws->ev_xback = nullptr;
+    if (ws->side_stream) cudaStreamDestroy(ws->side_stream);
+    if (ws->ev_fork) cudaEventDestroy(ws->ev_fork);
+    if (ws->ev_join) cudaEventDestroy(ws->ev_join);
+    ws->side_stream = nullptr;
+    ws->ev_fork = ws->ev_join = nullptr;
     ws->graph_exec = nullptr;
     ws->graph = nullptr;
     ws->cap_stream = nullptr;
@@ -606,6 +611,15 @@ tree_status_t tree_accel(TreeWorkspace *ws, const void *x, const void *m, int64_
     return tree_forces(ws, a, phi, 0, stream);
 }
 
+// The side stream and events a leapfrog step forks its walk groups onto
+// (created outside any stream capture).
+static tree_status_t ensure_side_stream(TreeWorkspace *ws) {
+    if (!ws->side_stream) TRY_CUDA(cudaStreamCreateWithFlags(&ws->side_stream, cudaStreamNonBlocking));
+    if (!ws->ev_fork) TRY_CUDA(cudaEventCreateWithFlags(&ws->ev_fork, cudaEventDisableTiming));
+    if (!ws->ev_join) TRY_CUDA(cudaEventCreateWithFlags(&ws->ev_join, cudaEventDisableTiming));
+    return TREE_OK;
+}
+
 // First part of a step: the first kick and the drift (Eqs. 2-3), fused with
 // the box of the new positions.  After it, x holds r^{n+1} and is only read.
 static tree_status_t leapfrog_begin(TreeWorkspace *ws, void *x, void *v, const void *m, void *a, double tau,
@@ -642,8 +656,15 @@ static tree_status_t leapfrog_finish(TreeWorkspace *ws, const void *x, void *v, 
     {
         PhaseScope ph(ws, TREE_PHASE_OCTREE, s);
         TRY_CUDA(launch_octree(ws, n, s));
-        TRY_CUDA(launch_groups(ws, n, s));
     }
+    // The walk groups need the octree only, and the gather and the moments do
+    // not need the groups: the groups run on the side stream meanwhile (their
+    // kernels wait on dependent loads, the moments on the FP64 pipe) and are
+    // joined before the walk.
+    TRY_CUDA(cudaEventRecord(ws->ev_fork, s));
+    TRY_CUDA(cudaStreamWaitEvent(ws->side_stream, ws->ev_fork, 0));
+    TRY_CUDA(launch_groups(ws, n, ws->side_stream));
+    TRY_CUDA(cudaEventRecord(ws->ev_join, ws->side_stream));
     ws->built = true;
     {
         PhaseScope ph(ws, TREE_PHASE_GATHER, s);
@@ -654,6 +675,7 @@ static tree_status_t leapfrog_finish(TreeWorkspace *ws, const void *x, void *v, 
         TRY_CUDA(launch_moments(ws, s));
     }
     ws->has_moments = true;
+    TRY_CUDA(cudaStreamWaitEvent(s, ws->ev_join, 0));
     WalkOut out{a, phi, v, 0.5 * tau};
     return walk(ws, kWalkForce, out, s);
 }
@@ -667,7 +689,9 @@ tree_status_t leapfrog_step(TreeWorkspace *ws, void *x, void *v, const void *m, 
     if (n == 0) return TREE_OK;
     if (!x || !v || !m || !a) return TREE_ERR_ARG;
     cudaStream_t s = as_stream(stream);
-    tree_status_t st = leapfrog_begin(ws, x, v, m, a, tau, n, s);
+    tree_status_t st = ensure_side_stream(ws);
+    if (st != TREE_OK) return st;
+    st = leapfrog_begin(ws, x, v, m, a, tau, n, s);
     if (st != TREE_OK) return st;
     return leapfrog_finish(ws, x, v, a, phi, tau, n, s);
 }
@@ -692,6 +716,8 @@ tree_status_t leapfrog_step_host(TreeWorkspace *ws, void *x, void *v, const void
     if (!ws->copy_stream) TRY_CUDA(cudaStreamCreateWithFlags(&ws->copy_stream, cudaStreamNonBlocking));
     if (!ws->ev_drift) TRY_CUDA(cudaEventCreateWithFlags(&ws->ev_drift, cudaEventDisableTiming));
     if (!ws->ev_xback) TRY_CUDA(cudaEventCreateWithFlags(&ws->ev_xback, cudaEventDisableTiming));
+    st = ensure_side_stream(ws);
+    if (st != TREE_OK) return st;
     cudaStream_t s = as_stream(stream);
     const size_t b3 = 3 * (size_t)n * rs, b1 = (size_t)n * rs;
     {
@@ -758,6 +784,8 @@ tree_status_t leapfrog_graph_capture(TreeWorkspace *ws, void *x, void *v, const 
     TRY_CUDA(cudaDeviceSynchronize());
     drop_graph(ws);
     if (!ws->cap_stream) TRY_CUDA(cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking));
+    st = ensure_side_stream(ws);
+    if (st != TREE_OK) return st;
     cudaStream_t cs = ws->cap_stream;
     // everything a step may do on the host first (the opening-criterion table)
     st = upload_mac(ws, cs);

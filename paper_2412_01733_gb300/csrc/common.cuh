@@ -140,6 +140,8 @@ struct TreeWorkspace {
     double *hs_diag = nullptr;
     cudaStream_t copy_stream = nullptr;  // copies back that overlap the rest of the step
     cudaEvent_t ev_drift = nullptr, ev_xback = nullptr;
+    cudaStream_t side_stream = nullptr;  // a leapfrog step's walk groups, beside its gather and moments
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // one captured leapfrog step (leapfrog_graph_capture)
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
