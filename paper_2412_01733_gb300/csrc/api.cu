@@ -654,17 +654,18 @@ static tree_status_t leapfrog_finish(TreeWorkspace *ws, const void *x, void *v, 
         TRY_CUDA(launch_sort(ws, n, s));
     }
     {
+        // The walk groups need the octree only, and the gather and the moments
+        // do not need the groups: the groups run on the side stream meanwhile
+        // (their kernels wait on dependent loads, the moments on the FP64 pipe)
+        // and are joined before the walk.  The phase's events, on s, time the
+        // octree; its launch count includes the groups.
         PhaseScope ph(ws, TREE_PHASE_OCTREE, s);
         TRY_CUDA(launch_octree(ws, n, s));
+        TRY_CUDA(cudaEventRecord(ws->ev_fork, s));
+        TRY_CUDA(cudaStreamWaitEvent(ws->side_stream, ws->ev_fork, 0));
+        TRY_CUDA(launch_groups(ws, n, ws->side_stream));
+        TRY_CUDA(cudaEventRecord(ws->ev_join, ws->side_stream));
     }
-    // The walk groups need the octree only, and the gather and the moments do
-    // not need the groups: the groups run on the side stream meanwhile (their
-    // kernels wait on dependent loads, the moments on the FP64 pipe) and are
-    // joined before the walk.
-    TRY_CUDA(cudaEventRecord(ws->ev_fork, s));
-    TRY_CUDA(cudaStreamWaitEvent(ws->side_stream, ws->ev_fork, 0));
-    TRY_CUDA(launch_groups(ws, n, ws->side_stream));
-    TRY_CUDA(cudaEventRecord(ws->ev_join, ws->side_stream));
     ws->built = true;
     {
         PhaseScope ph(ws, TREE_PHASE_GATHER, s);
