@@ -25,6 +25,8 @@
 // the lane and added to global FP64 accumulators with one atomic per
 // quantity per source per group; the target-side sums rotate through the
 // lanes with the targets.
+#include <cfloat>
+
 #include "common.cuh"
 
 namespace treegb {
@@ -58,14 +60,29 @@ template <typename Real> __device__ __forceinline__ Real rs_(Real x);
 template <> __device__ __forceinline__ float rs_<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rs_<double>(double x) { return rsqrt(x); }
 
+// 1/r of a pair.  Softened FP32 (SOFT, taken only when eps^2 is a normal FP32
+// number): r^2 >= eps^2 is never subnormal, so the PTX reciprocal square root
+// with subnormal inputs flushed serves, as in the walk's pair terms.
+// Otherwise the guarded form: a pair at r^2 = 0 contributes nothing.
+template <typename Real, bool SOFT>
+__device__ __forceinline__ Real inv_r(Real r2) {
+    if constexpr (SOFT && sizeof(Real) == 4) {
+        float y;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
+        return y;
+    } else {
+        return r2 > Real(0) ? rs_<Real>(r2) : Real(0);
+    }
+}
+
 // Derivatives of abar.a_PC + pb phi_PC for one (target, cell) pair.
 // y = target - R.  Outputs: gy (d/dy), mb (d/dM), qb (d/dQ stored components).
-template <typename Real, bool QUAD>
+template <typename Real, bool QUAD, bool SOFT>
 __device__ __forceinline__ void pc_vjp(Real yx, Real yy, Real yz, Real bx, Real by, Real bz, Real pb, Real Mc,
                                        const Real (&q)[6], Real eps2, Real &gx, Real &gy, Real &gz, Real &mb,
                                        Real (&qb)[6]) {
     const Real r2 = yx * yx + yy * yy + yz * yz + eps2;
-    const Real i1 = r2 > Real(0) ? rs_<Real>(r2) : Real(0);
+    const Real i1 = inv_r<Real, SOFT>(r2);
     const Real i2 = i1 * i1;
     const Real i3 = i1 * i2, i5 = i3 * i2, i7 = i5 * i2, i9 = i7 * i2;
     const Real yb = yx * bx + yy * by + yz * bz;
@@ -102,11 +119,11 @@ __device__ __forceinline__ void pc_vjp(Real yx, Real yy, Real yz, Real bx, Real 
 }
 
 // PP pair: d = source - target.  g as in the header; dm = d/dm_j (without G).
-template <typename Real>
+template <typename Real, bool SOFT>
 __device__ __forceinline__ void pp_vjp(Real dx, Real dy, Real dz, Real bx, Real by, Real bz, Real pb, Real mj,
                                        Real eps2, Real &gx, Real &gy, Real &gz, Real &dm) {
     const Real r2 = dx * dx + dy * dy + dz * dz + eps2;
-    const Real i1 = r2 > Real(0) ? rs_<Real>(r2) : Real(0);
+    const Real i1 = inv_r<Real, SOFT>(r2);
     const Real i3 = i1 * i1 * i1, i5 = i3 * i1 * i1;
     const Real db = dx * bx + dy * by + dz * bz;
     gx = mj * (bx * i3 - Real(3) * dx * db * i5 + pb * dx * i3);
@@ -115,7 +132,7 @@ __device__ __forceinline__ void pp_vjp(Real dx, Real dy, Real dz, Real bx, Real 
     dm = db * i3 - pb * i1;
 }
 
-template <typename Real, bool QUAD>
+template <typename Real, bool QUAD, bool SOFT>
 __global__ void __launch_bounds__(kAdjWarps * 32) k_force_vjp(const AdjArgs A) {
     using V4 = typename AdjVec<Real>::V4;
     using V2 = typename AdjVec<Real>::V2;
@@ -185,7 +202,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_force_vjp(const AdjArgs A) {
                     const V4 p = s_tp[w][32 * h + t];
                     const V4 b = s_tc[w][32 * h + t];
                     Real gx, gy, gz, mb, qb[6];
-                    pc_vjp<Real, QUAD>(p.x - ca.x, p.y - ca.y, p.z - ca.z, b.x, b.y, b.z, b.w, ca.w, cq, eps2, gx,
+                    pc_vjp<Real, QUAD, SOFT>(p.x - ca.x, p.y - ca.y, p.z - ca.z, b.x, b.y, b.z, b.w, ca.w, cq, eps2, gx,
                                        gy, gz, mb, qb);
                     tx += gx; ty += gy; tz += gz;
                     acc[0] += mb;
@@ -234,7 +251,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_force_vjp(const AdjArgs A) {
                     const V4 p = s_tp[w][32 * h + t];
                     const V4 b = s_tc[w][32 * h + t];
                     Real gx, gy, gz, dm;
-                    pp_vjp<Real>(sa.x - p.x, sa.y - p.y, sa.z - p.z, b.x, b.y, b.z, b.w, sa.w, eps2, gx, gy, gz,
+                    pp_vjp<Real, SOFT>(sa.x - p.x, sa.y - p.y, sa.z - p.z, b.x, b.y, b.z, b.w, sa.w, eps2, gx, gy, gz,
                                  dm);
                     tx -= gx; ty -= gy; tz -= gz;
                     gxs += gx; gys += gy; gzs += gz; dms += dm;
@@ -434,8 +451,19 @@ static cudaError_t adjoint_impl(TreeWorkspace *ws, const void *abar, const void 
     A.cap = cap;
     const unsigned gb = (unsigned)((A.ngroups + kAdjWarps - 1) / kAdjWarps);
     if (A.ngroups > 0) {
-        if (ws->p.order == 2) k_force_vjp<Real, true><<<gb, kAdjWarps * 32, 0, s>>>(A);
-        else k_force_vjp<Real, false><<<gb, kAdjWarps * 32, 0, s>>>(A);
+        const bool quad = ws->p.order == 2;
+        bool done = false;
+        if constexpr (sizeof(Real) == 4) {
+            if ((float)(ws->p.eps * ws->p.eps) >= FLT_MIN) {  // softened FP32 pairs (inv_r)
+                if (quad) k_force_vjp<Real, true, true><<<gb, kAdjWarps * 32, 0, s>>>(A);
+                else k_force_vjp<Real, false, true><<<gb, kAdjWarps * 32, 0, s>>>(A);
+                done = true;
+            }
+        }
+        if (!done) {
+            if (quad) k_force_vjp<Real, true, false><<<gb, kAdjWarps * 32, 0, s>>>(A);
+            else k_force_vjp<Real, false, false><<<gb, kAdjWarps * 32, 0, s>>>(A);
+        }
     }
     const int nbn = grid_for(ws->node_cap, 256, 152 * 8);
     for (int L = 0; L < kLevels; ++L)
