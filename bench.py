@@ -272,8 +272,9 @@ def run_ours(a):
     if not a.no_extras:
         # end to end through the C ABI with host-resident state (first among the extras, right after
         # the timed steps): leapfrog_step_host copies the state x, v, m, a up, runs the step and the
-        # diagnostics, and copies the new state x (under the tree build and walk), v, a and the
-        # diagnostics (which carry W) back
+        # diagnostics; the new x comes back by a copy under the tree build and walk, v and a by the
+        # walk's own stores into the (mapped, pinned) host arrays, the diagnostics (which carry W) by a
+        # copy after the step
         xh = x.cpu().pin_memory(); vh = v.cpu().pin_memory(); mh = m.cpu().pin_memory()
         ah = acc.cpu().pin_memory()
         dh = torch.empty(8, dtype=torch.float64).pin_memory()
@@ -301,7 +302,8 @@ def run_ours(a):
         out["e2e"] = {"value": world * n * a.steps / te, "unit": UNIT,
                       "h2d_bytes_per_step": 40 * n, "d2h_bytes_per_step": 36 * n + 64, "clocks": ck_e2e,
                       "api": "leapfrog_step_host (pinned host arrays; x copied back on a second stream under "
-                             "the tree build and walk)",
+                             "the tree build and walk; v and a written into the mapped host arrays by the walk "
+                             "itself, so d2h_after_walk_ms is the diagnostics' copy)",
                       "per_step": {k: round(v, 2) for k, v in split.items()}}
         # continue from the host state: the device arrays take it back
         x.copy_(xh); v.copy_(vh); acc.copy_(ah)

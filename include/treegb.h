@@ -141,7 +141,8 @@ typedef struct {
 #define TREE_PHASE_DIRECT 9  /* direct summation */
 #define TREE_PHASE_ADJOINT 10 /* tree_forces_adjoint */
 #define TREE_PHASE_H2D 11    /* leapfrog_step_host: copies of the state to the device */
-#define TREE_PHASE_D2H 12    /* leapfrog_step_host: copies back after the walk (x's copy overlaps the step) */
+#define TREE_PHASE_D2H 12    /* leapfrog_step_host: copies back after the walk (x's copy overlaps the step;
+                                with mapped host arrays only diag's) */
 #define TREE_NPHASES 13
 
 /* Fills *p with the defaults: G = 1, eps = 0.01, theta = 0.7, order = 2,
@@ -258,8 +259,11 @@ tree_status_t leapfrog_step(TreeWorkspace *ws, void *x, void *v, const void *m, 
  * particle of n_max in FP32, 88 in FP64).  The call copies x, v, m, a to the
  * device, runs the step, and copies x, v, a and phi back; x is final after
  * the drift, so its copy back runs on a second stream under the tree build
- * and walk.  diag (host double[8], or NULL) receives tree_diagnostics of the
- * new state.  Asynchronous on stream: the host arrays must not be used until
+ * and walk.  When v, a (and phi) are mapped page-locked memory (cudaHostAlloc,
+ * or cudaHostRegister with cudaHostRegisterMapped: cudaHostGetDevicePointer
+ * succeeds), the walk writes their new values into them directly as it goes
+ * and no copy back of them follows the walk.  diag (host double[8], or NULL)
+ * receives tree_diagnostics of the new state.  Asynchronous on stream: the host arrays must not be used until
  * the stream has run (the stream waits for every copy). */
 tree_status_t leapfrog_step_host(TreeWorkspace *ws, void *x, void *v, const void *m, void *a, void *phi,
                                  double tau, int64_t n, double *diag, void *stream);

@@ -644,7 +644,8 @@ static tree_status_t leapfrog_begin(TreeWorkspace *ws, void *x, void *v, const v
 // Rest of a step: the tree at r^{n+1} (Eq. 4) and the forces, written back
 // with the second kick (Eq. 5) fused in.
 static tree_status_t leapfrog_finish(TreeWorkspace *ws, const void *x, void *v, void *a, void *phi, double tau,
-                                     int64_t n, cudaStream_t s) {
+                                     int64_t n, cudaStream_t s, void *v_mirror = nullptr,
+                                     void *phi_mirror = nullptr) {
     {
         PhaseScope ph(ws, TREE_PHASE_KEYS, s);
         TRY_CUDA(launch_keys(ws, x, n, s));
@@ -678,6 +679,8 @@ static tree_status_t leapfrog_finish(TreeWorkspace *ws, const void *x, void *v, 
     ws->has_moments = true;
     TRY_CUDA(cudaStreamWaitEvent(s, ws->ev_join, 0));
     WalkOut out{a, phi, v, 0.5 * tau};
+    out.v_mirror = v_mirror;
+    out.phi_mirror = phi_mirror;
     return walk(ws, kWalkForce, out, s);
 }
 
@@ -736,7 +739,17 @@ tree_status_t leapfrog_step_host(TreeWorkspace *ws, void *x, void *v, const void
     TRY_CUDA(cudaStreamWaitEvent(ws->copy_stream, ws->ev_drift, 0));
     TRY_CUDA(cudaMemcpyAsync(x, ws->hs_x, b3, cudaMemcpyDeviceToHost, ws->copy_stream));
     TRY_CUDA(cudaEventRecord(ws->ev_xback, ws->copy_stream));
-    st = leapfrog_finish(ws, ws->hs_x, ws->hs_v, ws->hs_a, ws->hs_phi, tau, n, s);
+    // Where the caller's v, a (and phi) are mapped page-locked memory, the walk
+    // writes the new a, the kicked v and phi into them as it goes (besides the
+    // device copies that the diagnostics read), so nothing is left to copy
+    // back after it; otherwise they are copied back after the walk.
+    void *va = nullptr, *aa = nullptr, *pa = nullptr;
+    const bool mapped = cudaHostGetDevicePointer(&va, v, 0) == cudaSuccess &&
+                        cudaHostGetDevicePointer(&aa, a, 0) == cudaSuccess &&
+                        (!phi || cudaHostGetDevicePointer(&pa, phi, 0) == cudaSuccess);
+    if (!mapped) cudaGetLastError();  // not mapped: the copies back below
+    st = mapped ? leapfrog_finish(ws, ws->hs_x, ws->hs_v, aa, ws->hs_phi, tau, n, s, va, pa)
+                : leapfrog_finish(ws, ws->hs_x, ws->hs_v, ws->hs_a, ws->hs_phi, tau, n, s);
     if (st != TREE_OK) return st;
     if (diag) {
         PhaseScope ph(ws, TREE_PHASE_DIAG, s);
@@ -744,9 +757,11 @@ tree_status_t leapfrog_step_host(TreeWorkspace *ws, void *x, void *v, const void
     }
     {
         PhaseScope ph(ws, TREE_PHASE_D2H, s);
-        TRY_CUDA(cudaMemcpyAsync(v, ws->hs_v, b3, cudaMemcpyDeviceToHost, s));
-        TRY_CUDA(cudaMemcpyAsync(a, ws->hs_a, b3, cudaMemcpyDeviceToHost, s));
-        if (phi) TRY_CUDA(cudaMemcpyAsync(phi, ws->hs_phi, b1, cudaMemcpyDeviceToHost, s));
+        if (!mapped) {
+            TRY_CUDA(cudaMemcpyAsync(v, ws->hs_v, b3, cudaMemcpyDeviceToHost, s));
+            TRY_CUDA(cudaMemcpyAsync(a, ws->hs_a, b3, cudaMemcpyDeviceToHost, s));
+            if (phi) TRY_CUDA(cudaMemcpyAsync(phi, ws->hs_phi, b1, cudaMemcpyDeviceToHost, s));
+        }
         if (diag) TRY_CUDA(cudaMemcpyAsync(diag, ws->hs_diag, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
     }
     // the caller's stream completes only after x's copy has landed too

@@ -448,6 +448,8 @@ struct WalkOut {
     void *phi;          // [n] or NULL
     void *v;            // leapfrog: [3][n] velocities to kick, or NULL
     double half_tau;    // leapfrog kick
+    void *v_mirror = nullptr;    // also receives the kicked v (e.g. mapped host memory), or NULL
+    void *phi_mirror = nullptr;  // also receives phi, or NULL
 };
 cudaError_t launch_walk_f32(TreeWorkspace *ws, int mode, const WalkOut &out, cudaStream_t s);
 cudaError_t launch_walk_f64(TreeWorkspace *ws, int mode, const WalkOut &out, cudaStream_t s);

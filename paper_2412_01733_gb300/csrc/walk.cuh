@@ -44,6 +44,7 @@ struct WalkArgs {
     double G, eps, eps2;
     void *a, *phi, *v;
     double half_tau;
+    void *v2, *phi2;      // mirrors of the kicked v and of phi, or NULL
     int32_t stack_depth;
     uint4 *gstat;          // per group: {n_pc cells, n_pp particles, max stack, n_pp leaves}
     int32_t *dstatus;
@@ -722,12 +723,16 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 2 ? 4 : sizeof(Real) =
                 const int64_t n = A.n;
                 a[i] = ax; a[n + i] = ay; a[2 * n + i] = az;
                 if (A.phi) reinterpret_cast<Real *>(A.phi)[i] = ph;
+                if (A.phi2) reinterpret_cast<Real *>(A.phi2)[i] = ph;
                 if (A.v) {
                     Real *v = reinterpret_cast<Real *>(A.v);
                     const Real ht = (Real)A.half_tau;
-                    v[i] = fma(ht, ax, v[i]);
-                    v[n + i] = fma(ht, ay, v[n + i]);
-                    v[2 * n + i] = fma(ht, az, v[2 * n + i]);
+                    const Real vx = fma(ht, ax, v[i]), vy = fma(ht, ay, v[n + i]), vz = fma(ht, az, v[2 * n + i]);
+                    v[i] = vx; v[n + i] = vy; v[2 * n + i] = vz;
+                    if (A.v2) {
+                        Real *w = reinterpret_cast<Real *>(A.v2);
+                        w[i] = vx; w[n + i] = vy; w[2 * n + i] = vz;
+                    }
                 }
             }
         }
@@ -761,6 +766,8 @@ inline WalkArgs make_walk_args(TreeWorkspace *ws, const WalkOut &out) {
     a.phi = out.phi;
     a.v = out.v;
     a.half_tau = out.half_tau;
+    a.v2 = out.v_mirror;
+    a.phi2 = out.phi_mirror;
     a.stack_depth = ws->p.stack_depth;
     a.gstat = ws->gstat;
     a.dstatus = ws->dstatus;

@@ -453,10 +453,12 @@ def test_export_lists_groups_matches_full_export():
 
 
 @pytest.mark.parametrize("precision", ["f32", "f64"])
-def test_host_state_step_equals_device_step(precision):
-    """leapfrog_step_host (state in pinned host memory, copies inside the call,
-    x copied back under the walk) gives exactly the device-resident step: the
-    same kernels on the same data."""
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_state_step_equals_device_step(precision, pinned):
+    """leapfrog_step_host (state in host memory, copies up inside the call, x
+    copied back under the walk; v, a, phi written by the walk into mapped
+    page-locked arrays, or copied back after it from pageable ones) gives
+    exactly the device-resident step: the same kernels on the same data."""
     tg = _tg()
     n, tau = 20011, 0.005
     x, v, m = inputs.galaxy(n, 5)
@@ -465,9 +467,10 @@ def test_host_state_step_equals_device_step(precision):
     p = dict(eps=0.02, theta=0.6, order=2, leaf_cap=16, group_size=32, precision=precision)
     with tg.Workspace(n, **p) as wd, tg.Workspace(n, **p) as wh:
         a, phi = wd.accel(xg, mg)
-        xh, vh, mh, ah = (t.cpu().pin_memory() for t in (xg, vg, mg, a))
-        ph = torch.empty(n, dtype=dt).pin_memory()
-        dh = torch.empty(8, dtype=torch.float64).pin_memory()
+        host = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
+        xh, vh, mh, ah = (host(t.cpu()) for t in (xg, vg, mg, a))
+        ph = host(torch.empty(n, dtype=dt))
+        dh = host(torch.empty(8, dtype=torch.float64))
         diag = torch.empty(8, dtype=torch.float64, device="cuda")
         for _ in range(3):
             wd.leapfrog_step(xg, vg, mg, a, tau, phi=phi)
